@@ -1,0 +1,147 @@
+"""Python access to the CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path never does: it has no
+CPU fallback and fails when its CUDA library is missing.
+
+The oracle computes the sieve table of Jarai & Vatai (Definition "Sieve table,
+Segments", Sec. 1.3): bit j stands for the odd number 2(J0 + j) + 1 and is 1
+exactly when that number is composite.  See ``sieve_oracle.c`` for the passage
+each routine follows.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_oracle())
+        lib.oracle_isqrt.restype = _u64
+        lib.oracle_isqrt.argtypes = [_u64]
+        lib.oracle_base_primes.restype = _u64
+        lib.oracle_base_primes.argtypes = [_u64, ctypes.c_void_p, _u64]
+        lib.oracle_sieve_range.restype = ctypes.c_int
+        lib.oracle_sieve_range.argtypes = [_u64, _u64, _u64, ctypes.c_void_p, _u64, _u64,
+                                           ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_sieve.restype = ctypes.c_int
+        lib.oracle_sieve.argtypes = [_u32, _u64, _u64, ctypes.c_void_p, _u64, _u64,
+                                     ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_lemma_q.restype = _u64
+        lib.oracle_lemma_q.argtypes = [_u64, _u64, _u32]
+        lib.oracle_f_from_midpoint.restype = ctypes.c_int
+        lib.oracle_f_from_midpoint.argtypes = [_u32, _u64, _u64, _u32, ctypes.POINTER(_u64)]
+        lib.oracle_popcount.restype = _u64
+        lib.oracle_popcount.argtypes = [ctypes.c_void_p, _u64]
+        lib.oracle_is_composite_trial.restype = ctypes.c_int
+        lib.oracle_is_composite_trial.argtypes = [_u64]
+        lib.oracle_is_prime_mr.restype = ctypes.c_int
+        lib.oracle_is_prime_mr.argtypes = [_u64]
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def isqrt(x: int) -> int:
+    return int(_load().oracle_isqrt(x))
+
+
+class Base:
+    """The base P of Sec. 1.4: odd primes 3 <= p <= limit (ascending, uint32)."""
+
+    def __init__(self, limit: int):
+        lib = _load()
+        limit = min(int(limit), 0xFFFFFFFF)
+        cnt = lib.oracle_base_primes(limit, None, 0)
+        if cnt == 2**64 - 1:
+            raise MemoryError("oracle base primes")
+        arr = np.zeros(max(int(cnt), 1), dtype=np.uint32)
+        got = lib.oracle_base_primes(limit, arr.ctypes.data, cnt)
+        if got != cnt:
+            raise MemoryError("oracle base primes")
+        self.limit = limit
+        self.primes = arr[:cnt]
+
+
+_base_cache = {}
+
+
+def base_for(max_number: int) -> Base:
+    """A base covering every number up to max_number (cached by limit)."""
+    need = isqrt(max_number)
+    for lim, b in _base_cache.items():
+        if lim >= need:
+            return b
+    b = Base(need)
+    _base_cache.clear()
+    _base_cache[need] = b
+    return b
+
+
+def sieve_range(j0: int, nbits: int, seg_bits: int = 1 << 20, base: Base = None,
+                nthreads: int = None) -> np.ndarray:
+    """Table words (uint32, LSB-first) for absolute bit indices j0 .. j0+nbits-1."""
+    if nbits == 0:
+        return np.zeros(0, dtype=np.uint32)
+    if base is None:
+        base = base_for(2 * (j0 + nbits - 1) + 1)
+    out = np.zeros(nbits // 32, dtype=np.uint32)
+    rc = _load().oracle_sieve_range(j0, nbits, seg_bits, base.primes.ctypes.data,
+                                    len(base.primes), base.limit, out.ctypes.data,
+                                    nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_sieve_range failed with code %d" % rc)
+    return out
+
+
+def sieve(l: int, f: int, n: int, base: Base = None, nthreads: int = None) -> np.ndarray:
+    """The paper's table for (l, f, n): n*2^l bits, segments of 2^l bits."""
+    nbits = n << l
+    if base is None:
+        base = base_for(2 * ((f << l) + nbits - 1) + 1)
+    out = np.zeros(nbits // 32, dtype=np.uint32)
+    rc = _load().oracle_sieve(l, f, n, base.primes.ctypes.data, len(base.primes),
+                              base.limit, out.ctypes.data, nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_sieve failed with code %d" % rc)
+    return out
+
+
+def lemma_q(p: int, f: int, l: int) -> int:
+    return int(_load().oracle_lemma_q(p, f, l))
+
+
+def f_from_midpoint(l: int, n: int, mant: int, exp10: int) -> int:
+    out = _u64(0)
+    rc = _load().oracle_f_from_midpoint(l, n, mant, exp10, ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("oracle_f_from_midpoint failed with code %d" % rc)
+    return int(out.value)
+
+
+def popcount(words: np.ndarray) -> int:
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    return int(_load().oracle_popcount(words.ctypes.data, len(words)))
+
+
+def is_composite_trial(m: int) -> bool:
+    return bool(_load().oracle_is_composite_trial(m))
+
+
+def is_prime_mr(m: int) -> bool:
+    return bool(_load().oracle_is_prime_mr(m))
+
+
+def get_bit(words: np.ndarray, j: int) -> int:
+    return int((int(words[j >> 5]) >> (j & 31)) & 1)
