@@ -1,0 +1,362 @@
+"""Benchmark: odd numbers sieved per second on GB300, with roofline and CPU baseline.
+
+Default workload (one GPU): l=20, n=8192 segments (2^34 consecutive numbers,
+2^33 odd ones) with the midpoint at 10^15, the paper's (l, f, n) interface.
+--workload c3 runs l=20, n=32768 around 2^60 (the large-prime-dominated case);
+--workload batch runs the 4096 seeded requests of uneven length and magnitude.
+Under torchrun each rank sieves its own interval of the same size (the next n
+segments): weak scaling, no collective on the data path.
+
+Prints one JSON line.  `value` is device-timed throughput (CUDA events on the
+launching stream, outputs resident in HBM); `e2e` is the same metric through the
+C ABI with the table delivered to pinned host memory.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c2": dict(name="l20_n8192_mid1e15", l=20, n=8192, mant=1, exp10=15),
+    "c3": dict(name="l20_n32768_mid2p60", l=20, n=32768, mant=1 << 60, exp10=0),
+    "c1": dict(name="l15_f0_n1024", l=15, n=1024, f=0),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-plain", action="store_true", help="also time the batch as per-request calls")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# exact algorithmic counts for the roofline
+# ---------------------------------------------------------------------------
+def wheel_marks(J0, N, primes):
+    """Marks the device executes for these primes on [J0, J0+N): odd multiples
+    m = p*c, c coprime to 15, m >= p^2 (Sec. 1.4, Sec. 3.2.1); closed form per prime."""
+    import numpy as np
+    p = np.asarray(primes, dtype=np.int64)
+    if len(p) == 0:
+        return 0
+    half = (p - 1) // 2
+    first = J0 + ((half - J0) % p)
+    jsq = (p * p - 1) // 2
+    J1 = np.maximum(first, jsq)
+    Jend = J0 + N - 1
+    Jlast = Jend - ((Jend - half) % p)
+    ok = J1 <= Jlast
+    c1 = (2 * J1 + 1) // p
+    c2 = (2 * Jlast + 1) // p
+    R = np.array([1, 7, 11, 13, 17, 19, 23, 29])
+
+    def F(x):  # odd c <= x, coprime to 15
+        q, r = np.divmod(x, 30)
+        return 8 * q + (R[None, :] <= r[:, None]).sum(axis=1)
+
+    cnt = F(c2) - F(c1 - 1)
+    return int(cnt[ok].sum())
+
+
+def base_primes_upto(x):
+    import numpy as np
+    x = int(x)
+    s = np.ones(x // 2 + 1, dtype=bool)
+    s[0] = False
+    for i in range(1, (int(x ** 0.5) + 1) // 2 + 1):
+        if s[i]:
+            p = 2 * i + 1
+            s[(p * p) // 2::p] = False
+    return 2 * np.nonzero(s)[0] + 1
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world, wl):
+    """The oracle (CPU) on a bounded sample of the workload, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    l, n = wl["l"], wl["n"]
+    f = wl.get("f")
+    if f is None:
+        f = oracle.f_from_midpoint(l, n, wl["mant"], wl["exp10"])
+    sample = 64 if args.workload != "c1" else n
+    base = oracle.base_for(2 * ((f + n) << l) - 1)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.sieve(l, f, min(sample, 8), base=base, nthreads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.sieve(l, f + (k * sample) % max(1, n - sample + 1), sample, base=base, nthreads=cores)
+    dt = time.perf_counter() - t0
+    val = args.steps * (sample << l) / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "odd numbers sieved/s", "value": val,
+        "unit": "odd numbers/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["name"], "l": l, "f": f, "n": n},
+        "cpu_baseline": {"value": val, "unit": "odd numbers/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of %d segments (2^%d bits each) per step, all host cores" % (sample, n, l)},
+        "e2e": {"value": val, "unit": "odd numbers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(wl, f):
+    import oracle
+    l, n = wl["l"], wl["n"]
+    cores = os.cpu_count() or 1
+    sample = min(n, 1024 if l <= 16 else 256)
+    base = oracle.base_for(2 * ((f + n) << l) - 1)
+    t0 = time.perf_counter()
+    oracle.sieve(l, f, sample, base=base, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": (sample << l) / dt, "unit": "odd numbers/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d segments (2^%d bits each), %.2f s on %d threads"
+                      % (sample, n, l, dt, cores)}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    wl = WORKLOADS.get(args.workload)
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank, world, wl)
+        return
+
+    import torch
+    from paper_1111_3297_gb300 import build
+    build.build_library()
+    from paper_1111_3297_gb300 import sieve as S
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    l, n = wl["l"], wl["n"]
+    f0 = wl.get("f")
+    if f0 is None:
+        f0 = S.sieve_f_from_midpoint(l, n, wl["mant"], wl["exp10"])
+    f = f0 + rank * n  # weak scaling: each rank its own n segments
+    N = n << l
+    J0 = f << l
+    vmax = 2 * ((f0 + world * n) << l)
+    ctx = S.sieve_init(local, max_v=vmax)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+
+    tuned = None
+    if not args.no_autotune:
+        tuned = S.sieve_autotune(ctx, l, f, n)
+    r_atom = S.sieve_probe_smem_atomics(local)
+
+    for _ in range(max(3, args.warmup)):
+        S.sieve_segments(ctx, l, f, n, out)
+    S.sieve_sync(ctx)
+
+    # ---- timed region: K steps, per-kernel CUDA events inside the library ----
+    S.sieve_profile_enable(ctx, True)
+    S.sieve_profile_read(ctx)  # reset
+    clocks = Clocks(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        S.sieve_segments(ctx, l, f, n, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = S.sieve_profile_read(ctx)
+    S.sieve_profile_enable(ctx, False)
+    S.sieve_sync(ctx)
+    ms_max = ms
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max * 1e-3)
+
+    composites = S.sieve_count(ctx, out, N)
+
+    # ---- end to end: the table delivered to pinned host memory ----
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(N // 32, dtype=torch.int32).pin_memory()
+        S.sieve_segments_host(ctx, l, f, n, host)  # warm (plans, staging)
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 5))
+        for _ in range(ksteps):
+            S.sieve_segments_host(ctx, l, f, n, host)
+        dt = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([dt], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * N * ksteps / dt, "unit": "odd numbers/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": N // 8, "steps": ksteps}
+        del host
+
+    # ---- roofline of the dominant kernel ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    tune = S.sieve_get_tuning(ctx, 0 if vmax < 2**40 else 1 if vmax < 2**50 else 2 if vmax < 2**56 else 3)
+    if tuned:
+        tune = tuned
+    import numpy as np
+    plimit = int(np.floor(np.sqrt(float(2 * (J0 + N) - 1))))
+    primes = base_primes_upto(min(plimit, tune["medium_max"]))
+    presieve_max = [13, 23, 31, 41, 47, 59, 67, 73, 83, 97, 103, 109, 127][tune["presieve_groups"] - 1]
+    medium = primes[(primes > presieve_max) & (primes <= min(plimit, tune["medium_max"]))]
+    h_medium = wheel_marks(J0, N, medium)  # per step
+    steps = args.steps
+    h_large = prof["large_hits"] / steps
+    t_tile = prof["ms"][S.K_TILE] / steps * 1e-3
+    t_scatter = prof["ms"][S.K_SCATTER] / steps * 1e-3
+    n_tile = prof["launches"][S.K_TILE] / steps
+    n_scatter = prof["launches"][S.K_SCATTER] / steps
+    marks = h_medium + h_large
+    tile_bytes = N / 8 + 4 * h_large
+    scatter_bytes = 4 * h_large + 12 * prof["prime_reads"] / steps
+    kernels = {
+        "k_tile": {"ms_per_step": t_tile * 1e3, "launches_per_step": n_tile,
+                   "marks": marks, "atomics_per_s": marks / t_tile if t_tile else None,
+                   "hbm_bytes": tile_bytes, "hbm_gbs": tile_bytes / t_tile / 1e9 if t_tile else None},
+        "k_scatter": {"ms_per_step": t_scatter * 1e3, "launches_per_step": n_scatter,
+                      "hits": h_large, "hbm_bytes": scatter_bytes,
+                      "hbm_gbs": scatter_bytes / t_scatter / 1e9 if t_scatter else None},
+    }
+    if t_tile >= t_scatter:
+        ach = marks / t_tile / 1e9
+        roof = {"kernel": "k_tile", "bound": "smem_atomic", "achieved": ach, "peak": r_atom / 1e9,
+                "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": None,
+                "peak_source": "measured in this run (conflict-free shared atomicOr probe)",
+                "hbm_achieved_gbs": tile_bytes / t_tile / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": tile_bytes / t_tile / 1e9 / hbm_peak}
+    else:
+        ach = scatter_bytes / t_scatter / 1e9
+        roof = {"kernel": "k_scatter", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    # step-level roofline: the slower of HBM bytes at peak and marks at the atomic peak
+    step_s = ms_max * 1e-3 / steps
+    b_alg = N / 8 + 16 * h_large + 4 * prof["prime_reads"] / steps
+    t_roof = max(b_alg / (hbm_peak * 1e9), marks / r_atom)
+    step_roof = {"t_roof_ms": t_roof * 1e3, "t_step_ms": step_s * 1e3, "frac": t_roof / step_s,
+                 "bytes_alg": b_alg, "marks": marks, "bound": "hbm" if b_alg / (hbm_peak * 1e9) >= marks / r_atom
+                 else "smem_atomic"}
+
+    base_line = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base_line = cpu_baseline(wl, f0)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": "odd numbers sieved/s", "value": value, "unit": "odd numbers/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["name"], "l": l, "f": f0, "n": n, "parallelism": "interval shards x%d" % world,
+                       "l2": "working set larger than L2 (table %d MiB + buckets)" % (N // 8 // 2**20),
+                       "tuning": tune},
+            "gpu_launches": int(sum(prof["launches"])),
+            "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+            "cpu_baseline": base_line, "e2e": e2e, "clocks": clk,
+            "composites": composites, "smem_atomic_peak_per_s": r_atom,
+        }), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * gbsieve — odd-only segmented sieve of Eratosthenes on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libgbsieve.so.  Plain pointers and sizes only.  Device pointers are
+ * CUDA device addresses (e.g. from cudaMalloc or a torch CUDA tensor); host
+ * pointers are ordinary process memory.  Streams are cudaStream_t values
+ * (0 = the legacy default stream).  Every call that takes a stream enqueues its
+ * device work asynchronously on that stream unless the comment says it waits.
+ *
+ * The table (Jarai & Vatai, "Cache optimized linear sieve", Definition "Sieve
+ * table, Segments", Sec. 1.3): for parameters l, f, n (Sec. 1.2.1) it has
+ * n*2^l bits; bit j stands for the odd number 2(f*2^l + j) + 1 and is 1 exactly
+ * when that number is composite (so 1 and every prime read 0).  The numbers
+ * covered are u = f*2^(l+1)+1 .. v = (f+n)*2^(l+1).
+ * Layout: bit j is bit (j % 32) of 32-bit word j / 32 (least significant bit
+ * first), words consecutive in memory.
+ *
+ * Errors: argument and allocation errors are returned at once.  Errors raised
+ * on the device (a bucket overflow beyond the backstop, a bounded wait that ran
+ * out) are recorded in the context and returned by the next call that waits
+ * on the stream (sieve_count, sieve_sync, sieve_segments_host).  Functions are
+ * not thread-safe on one context, except the server functions, which lock.
+ */
+#ifndef GBSIEVE_H
+#define GBSIEVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sieve_stream; /* same type as cudaStream_t */
+typedef struct sieve_ctx sieve_ctx;
+
+typedef enum {
+    SIEVE_OK = 0,
+    SIEVE_EINVAL = 1,    /* bad argument (null pointer, l out of range, n = 0, misaligned) */
+    SIEVE_ERANGE = 2,    /* numbers beyond 2^64, or sqrt(v) beyond the context's base */
+    SIEVE_ENOMEM = 3,    /* device or host allocation failed / over the memory budget */
+    SIEVE_ECUDA = 4,     /* a CUDA runtime call failed */
+    SIEVE_ETIMEOUT = 5,  /* a bounded device or host wait ran out */
+    SIEVE_EBUSY = 6,     /* server queue full / resource in use */
+    SIEVE_EOVERFLOW = 7  /* large-prime bucket overflow beyond the backstop list */
+} sieve_status;
+
+/* Text for a status code (static storage). */
+const char *sieve_strerror(sieve_status s);
+
+/*
+ * Create a context on CUDA device `device`, able to sieve any interval whose
+ * largest number is <= max_v.  Builds the base of Sec. 1.4 (Definition "base":
+ * the odd primes p <= sqrt(max_v)) on the device and keeps it resident with one
+ * 64-bit reduction constant per prime.  mem_budget bounds the device memory the
+ * context uses for large-prime buckets (0 = 8 GiB).  Waits for the device.
+ * On success *ctx owns all its device memory until sieve_destroy.
+ */
+sieve_status sieve_init(sieve_ctx **ctx, int device, uint64_t max_v, size_t mem_budget);
+
+/* Free the context and everything it owns.  NULL is ignored. */
+void sieve_destroy(sieve_ctx *ctx);
+
+/*
+ * The sieve table for (l, f, n) (Sec. 1.2.1, Sec. 1.3) into caller-owned device
+ * memory dev_bits of n*2^(l-5) uint32 words (16-byte aligned).  5 <= l <= 40,
+ * n >= 1, (f+n)*2^(l+1) < 2^64, and isqrt(v-1) within the context's base, else
+ * SIEVE_EINVAL / SIEVE_ERANGE.  Asynchronous on `stream`; dev_bits must stay
+ * valid until the stream reaches the work.  The segment size the device uses
+ * internally is the autotuner's choice; the bits do not depend on it.
+ */
+sieve_status sieve_segments(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
+                            uint32_t *dev_bits, sieve_stream stream);
+
+/*
+ * As sieve_segments, with f chosen from the midpoint M = mant * 10^exp10 as in
+ * Sec. 1.2.1 (the midpoint input): f = max(0, floor(M / 2^(l+1)) - floor(n/2)).
+ */
+sieve_status sieve_f_from_midpoint(uint32_t l, uint64_t n, uint64_t mant, uint32_t exp10,
+                                   uint64_t *f_out);
+sieve_status sieve_segments_midpoint(sieve_ctx *ctx, uint32_t l, uint64_t mant, uint32_t exp10,
+                                     uint64_t n, uint32_t *dev_bits, sieve_stream stream);
+
+/*
+ * End-to-end form of sieve_segments: the table lands in caller-owned HOST memory
+ * host_bits (n*2^(l-5) words; pinned memory copies fastest).  The context stages
+ * the table on the device and copies it back window by window, overlapping the
+ * copies with the sieving.  Waits until the table is in host_bits.
+ */
+sieve_status sieve_segments_host(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
+                                 uint32_t *host_bits, sieve_stream stream);
+
+/*
+ * Number of 1 bits (composites) in the first nbits bits of the device table
+ * dev_bits (nbits % 32 == 0).  Waits for `stream` and writes *host_count.
+ * Primes in the table's range = nbits - composites - (1 if the table starts at
+ * the number 1, since 1 is neither).
+ */
+sieve_status sieve_count(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t nbits,
+                         uint64_t *host_count, sieve_stream stream);
+
+/* Wait for `stream` and report any device-side error recorded since the last wait. */
+sieve_status sieve_sync(sieve_ctx *ctx, sieve_stream stream);
+
+/*
+ * Batched form: `count` independent interval requests in one launch sequence.
+ * Request r covers absolute bit indices j0 .. j0+nbits-1 (numbers 2J+1), with
+ * j0 and nbits multiples of 32 and nbits >= 32; its table goes to
+ * dev_arena + out_word_off (words, caller-owned device memory) and its composite
+ * count to dev_counts[r] (uint64, overwritten).  Bits are those of
+ * sieve_segments for the same numbers.  Asynchronous; host_reqs may be reused
+ * when the call returns.  The launch sequence is captured in a CUDA graph that
+ * is replayed when the same request list is submitted again.
+ */
+typedef struct {
+    uint64_t j0;
+    uint64_t nbits;
+    uint64_t out_word_off;
+} sieve_req;
+
+sieve_status sieve_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t count,
+                         uint32_t *dev_arena, uint64_t *dev_counts, sieve_stream stream);
+
+/*
+ * Tuning of the device path (none of it changes the bits):
+ *   tile_log2     on-chip segment size 2^tile_log2 bits (12..20), one CTA per tile;
+ *   presieve_groups  how many small-prime pattern groups pre-sieve a tile
+ *                 (1..13; group 1 = {3,5,7,11,13}, up to 127 with 13 groups);
+ *   coop_max      primes below this are struck by a whole warp, 32 multiples at a time;
+ *   medium_max    primes up to this are struck inside the tile kernel; larger
+ *                 primes go through the large-prime buckets;
+ *   window_tiles  tiles per bucket window (scatter flush domain), 16..1024;
+ *   epoch_tiles   tiles whose buckets are filled by one scatter pass (multiple of
+ *                 window_tiles, bounded by the memory budget).
+ */
+typedef struct {
+    uint32_t tile_log2;
+    uint32_t presieve_groups;
+    uint32_t coop_max;
+    uint32_t medium_max;
+    uint32_t window_tiles;
+    uint32_t epoch_tiles;
+} sieve_tuning;
+
+/* Tuning classes: by the magnitude of the interval's largest number. */
+#define SIEVE_TUNE_CLASSES 4 /* < 2^40, < 2^50, < 2^56, >= 2^56 */
+sieve_status sieve_get_tuning(sieve_ctx *ctx, uint32_t cls, sieve_tuning *out);
+sieve_status sieve_set_tuning(sieve_ctx *ctx, uint32_t cls, const sieve_tuning *in);
+
+/*
+ * Autotune the class that (l, f, n) falls in: time candidate tunings on a
+ * sample of that interval (writing scratch device memory the context owns),
+ * keep the fastest in the context and return it in *out.  Waits for the device.
+ */
+sieve_status sieve_autotune(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
+                            sieve_tuning *out, sieve_stream stream);
+
+/*
+ * Autotune the batched form on a request list (as for sieve_batch): time candidate
+ * tile sizes (2^16..2^20 bits), medium/large thresholds and windows on the
+ * actual requests, writing dev_arena / dev_counts as sieve_batch would; the
+ * fastest becomes the tuning sieve_batch uses from then on.  Waits for the device.
+ */
+sieve_status sieve_autotune_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t count,
+                                  uint32_t *dev_arena, uint64_t *dev_counts, sieve_tuning *out,
+                                  sieve_stream stream);
+
+/* Base primes resident in the context (device pointer, ascending) and their count. */
+sieve_status sieve_base_info(sieve_ctx *ctx, const uint32_t **dev_primes, uint64_t *count,
+                             uint64_t *limit);
+
+/*
+ * Per-kernel timing of the device work of later calls, by CUDA events on the
+ * call's stream (enable = 1 turns it on, 0 off).  sieve_profile_read waits for the
+ * stream and returns, per kernel kind, the launches and the summed milliseconds
+ * since the last read, plus work counters (hits emitted, bytes moved).
+ */
+typedef struct {
+    uint64_t launches[8];    /* by kind, see SIEVE_K_* */
+    double ms[8];
+    uint64_t tiles;          /* tiles sieved */
+    uint64_t bits;           /* table bits written */
+    uint64_t large_hits;     /* bucket entries emitted (large-prime hits) */
+    uint64_t medium_marks;   /* estimated in-tile marks by medium primes */
+    uint64_t prime_reads;    /* (prime, window) first-hit computations in the scatter */
+} sieve_profile;
+#define SIEVE_K_TILE 0
+#define SIEVE_K_SCATTER 1
+#define SIEVE_K_COUNT 2
+#define SIEVE_K_RESET 3
+#define SIEVE_K_COPY 4
+sieve_status sieve_profile_enable(sieve_ctx *ctx, int enable);
+sieve_status sieve_profile_read(sieve_ctx *ctx, sieve_profile *out, sieve_stream stream);
+
+/*
+ * Micro-benchmark of the device's shared-memory atomic OR rate (the denominator
+ * of the in-tile marking roofline): every SM runs CTAs that OR single bits into
+ * random words of a shared array; returns atomics per second over the whole GPU.
+ * Waits for the device.
+ */
+sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s);
+
+/*
+ * Serving: a request loop with continuous batching.  Requests are submitted
+ * from any host thread; a scheduler thread admits them while the in-flight
+ * tables plus bucket memory stay within mem_cap bytes and at most max_inflight
+ * batches run, groups the admitted ones into a batch and launches it on the
+ * next of its streams, so that batches overlap on the device.  Base primes and
+ * bucket pools stay resident.  Results are read with sieve_server_poll: the
+ * composite count, a device pointer to the request's table inside the server's
+ * memory (valid until sieve_server_release) and the completion time.
+ */
+typedef struct sieve_server sieve_server;
+typedef struct {
+    uint64_t id;            /* as returned by submit */
+    uint64_t j0, nbits;
+    uint64_t composites;
+    const uint32_t *dev_bits;
+    double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock */
+    int status;             /* sieve_status of the request */
+} sieve_result;
+
+sieve_status sieve_server_create(sieve_ctx *ctx, size_t mem_cap, uint32_t max_inflight,
+                                 sieve_server **srv);
+sieve_status sieve_server_submit(sieve_server *srv, uint64_t j0, uint64_t nbits, uint64_t *id);
+/* Up to max results that completed since the last poll; *n receives how many.
+ * timeout_ms > 0 waits (bounded) for at least one. */
+sieve_status sieve_server_poll(sieve_server *srv, sieve_result *out, uint32_t max, uint32_t *n,
+                               uint32_t timeout_ms);
+sieve_status sieve_server_release(sieve_server *srv, uint64_t id);
+double sieve_server_now(sieve_server *srv);
+/* Stop the scheduler after the requests already submitted have completed. */
+void sieve_server_destroy(sieve_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSIEVE_H */

@@ -1,0 +1,964 @@
+// C ABI of the GB300 sieve: context (resident base and scratch), planner,
+// executor (direct launches or a replayed CUDA graph), and the entry points of
+// include/gbsieve.h.
+#include "gbsieve.h"
+#include "sieve_internal.cuh"
+#include "host_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+using namespace gbs;
+
+namespace gbs {
+
+// ---------------------------------------------------------------------------
+// small exact integer helpers
+// ---------------------------------------------------------------------------
+uint64_t isqrt_u64(uint64_t x)
+{
+    if (x < 2) return x;
+    uint64_t r = (uint64_t)std::sqrt((double)x);
+    while ((unsigned __int128)r * r > x) --r;
+    while ((unsigned __int128)(r + 1) * (r + 1) <= x) ++r;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// pre-sieve groups (Sec. 3.1: small primes applied as bit masks; here as
+// periodic patterns, several primes merged into one pattern as in the paper's
+// 3*11 and 5*7 merge)
+// ---------------------------------------------------------------------------
+static const uint32_t kGroups[kMaxPresieveGroups][5] = {
+    {3, 5, 7, 11, 13}, {17, 19, 23, 0, 0}, {29, 31, 0, 0, 0},  {37, 41, 0, 0, 0},  {43, 47, 0, 0, 0},
+    {53, 59, 0, 0, 0}, {61, 67, 0, 0, 0},  {71, 73, 0, 0, 0},  {79, 83, 0, 0, 0},  {89, 97, 0, 0, 0},
+    {101, 103, 0, 0, 0}, {107, 109, 0, 0, 0}, {113, 127, 0, 0, 0}};
+
+void build_presieve(PresieveTable &t)
+{
+    t.words.clear();
+    for (int g = 0; g < kMaxPresieveGroups; ++g) {
+        uint32_t P = 1, maxp = 0;
+        for (int i = 0; i < 5 && kGroups[g][i]; ++i) {
+            P *= kGroups[g][i];
+            maxp = kGroups[g][i];
+        }
+        t.modulus[g] = P;
+        t.maxp[g] = maxp;
+        t.word_off[g] = (uint32_t)t.words.size();
+        const uint32_t nw = (P + 64 + 31) / 32 + 1;
+        std::vector<uint32_t> w(nw, 0);
+        for (uint32_t rho = 0; rho < 32 * nw; ++rho) {
+            const uint32_t r = rho % P;  // the pattern repeats with period P
+            bool hit = false;
+            for (int i = 0; i < 5 && kGroups[g][i]; ++i)
+                if ((2 * (uint64_t)r + 1) % kGroups[g][i] == 0) hit = true;
+            if (hit) w[rho / 32] |= 1u << (rho % 32);
+        }
+        t.words.insert(t.words.end(), w.begin(), w.end());
+    }
+}
+
+}  // namespace gbs
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+const char *sieve_strerror(sieve_status s)
+{
+    switch (s) {
+    case SIEVE_OK: return "ok";
+    case SIEVE_EINVAL: return "invalid argument";
+    case SIEVE_ERANGE: return "numbers out of range for the context";
+    case SIEVE_ENOMEM: return "out of memory";
+    case SIEVE_ECUDA: return "CUDA runtime error";
+    case SIEVE_ETIMEOUT: return "timed out";
+    case SIEVE_EBUSY: return "busy";
+    case SIEVE_EOVERFLOW: return "large-prime bucket overflow";
+    }
+    return "unknown status";
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s:%d %s: %s", \
+                          __FILE__, __LINE__, #call, cudaGetErrorString(e_));         \
+            return SIEVE_ECUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+namespace gbs {
+char g_last_cuda_error[512];
+
+uint32_t prime_count_le(const sieve_ctx *c, uint64_t x)
+{
+    return (uint32_t)(std::upper_bound(c->h_primes.begin(), c->h_primes.end(), (uint64_t)std::min<uint64_t>(x, 0xFFFFFFFFull)) -
+                      c->h_primes.begin());
+}
+
+// sum of 1/p over base indices [a, b): an upper bound from the block prefix table
+double inv_sum(const sieve_ctx *c, uint32_t a, uint32_t b)
+{
+    if (b <= a) return 0.0;
+    const uint32_t blk = kInvBlock;
+    const uint32_t ba = a / blk, bb = (b + blk - 1) / blk;
+    return c->h_inv_prefix[std::min<size_t>(bb, c->h_inv_prefix.size() - 1)] - c->h_inv_prefix[ba];
+}
+
+uint32_t tune_class(uint64_t vlast)
+{
+    const int lg = 63 - __builtin_clzll(vlast | 1);
+    return lg < 40 ? 0 : lg < 50 ? 1 : lg < 56 ? 2 : 3;
+}
+
+sieve_tuning default_tuning(uint32_t cls)
+{
+    sieve_tuning t;
+    t.tile_log2 = 20;
+    t.presieve_groups = 6;
+    t.coop_max = 1u << 13;
+    t.medium_max = 1u << 20;
+    t.window_tiles = 1024;
+    t.epoch_tiles = 4096;
+    if (cls == 0) t.tile_log2 = 18, t.medium_max = 1u << 18, t.coop_max = 1u << 11;
+    return t;
+}
+
+bool tuning_valid(const sieve_tuning &t)
+{
+    return t.tile_log2 >= 12 && t.tile_log2 <= 20 && t.presieve_groups >= 1 &&
+           t.presieve_groups <= (uint32_t)kMaxPresieveGroups && t.medium_max <= (1u << 28) &&
+           t.window_tiles >= 1 && t.window_tiles <= kScatterMaxTiles &&
+           ((uint64_t)t.window_tiles << t.tile_log2) <= (1ull << 30) && t.epoch_tiles >= t.window_tiles &&
+           t.epoch_tiles <= 65535;
+}
+
+}  // namespace gbs
+
+static sieve_status alloc_dev(void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return SIEVE_ENOMEM;
+    }
+    return SIEVE_OK;
+}
+
+// grow-only scratch buffer; *gen is bumped when the buffer moves, which makes
+// captured graphs that point at the old buffer re-capture
+static sieve_status ensure(void **p, size_t *have, size_t need, uint64_t *gen)
+{
+    if (*have >= need && *p) return SIEVE_OK;
+    if (gen) ++*gen;
+    if (*p) cudaDeviceSynchronize();  // in-flight work may still use it
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    size_t n = std::max(need, (size_t)4096);
+    sieve_status s = alloc_dev(p, n);
+    if (s == SIEVE_OK) *have = n;
+    return s;
+}
+
+namespace gbs {
+
+sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap)
+{
+    s.pool_entries = pool_entries;
+    s.ovf_cap = ovf_cap;
+    sieve_status r = alloc_dev((void **)&s.d_small, 64);
+    if (!r) r = alloc_dev((void **)&s.d_err, 16);
+    if (!r) r = alloc_dev((void **)&s.d_acc, 64);
+    if (!r) r = alloc_dev((void **)&s.d_ovf, (size_t)ovf_cap * 8);
+    if (r) return r;
+    CK(cudaMemset(s.d_small, 0, 64));
+    CK(cudaMemset(s.d_err, 0, 16));
+    CK(cudaMemset(s.d_acc, 0, 64));
+    return SIEVE_OK;
+}
+
+void scratch_free(Scratch &s)
+{
+    for (void *p : {(void *)s.d_bkt, (void *)s.d_bkt_cnt, (void *)s.d_ovf, (void *)s.d_small, (void *)s.d_err,
+                    (void *)s.d_acc})
+        if (p) cudaFree(p);
+    s = Scratch{};
+}
+
+sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles)
+{
+    if (pool_entries > s.pool_entries) return SIEVE_ENOMEM;
+    sieve_status r = ensure((void **)&s.d_bkt, &s.bkt_bytes, (size_t)pool_entries * 4 + 64, &s.gen);
+    if (r) return r;
+    return ensure((void **)&s.d_bkt_cnt, &s.bkt_cnt_bytes, (size_t)max_epoch_tiles * 4 + 64, &s.gen);
+}
+
+// ---------------------------------------------------------------------------
+// planner
+// ---------------------------------------------------------------------------
+// Every request is cut into tiles of 2^tile_log2 bits (the last one ragged).
+// Requests whose largest prime exceeds medium_max also get large-prime
+// buckets: their tiles are grouped into scatter groups (<= window_tiles tiles,
+// runs of one request form a scatter unit) and groups into epochs whose bucket
+// capacity fits the pool.  Per epoch: scatter launch, then tile launch.
+std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tuning t, uint64_t pool_cap_in)
+{
+    std::unique_ptr<Plan> P(new Plan());
+    P->tune = t;
+    const uint32_t bt = t.tile_log2;
+    const uint64_t B = 1ull << bt;
+    P->ps.ngroups = t.presieve_groups;
+    for (int g = 0; g < kMaxPresieveGroups; ++g) {
+        P->ps.modulus[g] = c->pre.modulus[g];
+        P->ps.word_off[g] = c->pre.word_off[g];
+    }
+    P->ps.max_prime = c->pre.maxp[t.presieve_groups - 1];
+    P->med_lo = prime_count_le(c, P->ps.max_prime);
+    P->coop_hi = std::max(P->med_lo, prime_count_le(c, t.coop_max));
+    const uint32_t large_lo = std::max(P->med_lo, prime_count_le(c, t.medium_max));
+    const uint64_t pool_cap = pool_cap_in ? pool_cap_in : c->scr.pool_entries;
+
+    struct ReqInfo {
+        uint32_t med_hi, large_hi;
+        double inv;
+        uint32_t nsmall_large;  // large primes below the tile size (several hits per tile)
+        uint32_t plimit;
+    };
+    std::vector<ReqInfo> info(reqs.size());
+    for (size_t r = 0; r < reqs.size(); ++r) {
+        const uint64_t vlast = 2 * (reqs[r].j0 + reqs[r].nbits - 1) + 1;
+        const uint32_t plim = (uint32_t)isqrt_u64(vlast);
+        ReqInfo &ri = info[r];
+        ri.plimit = plim;
+        ri.med_hi = std::max(P->med_lo, prime_count_le(c, std::min<uint64_t>(t.medium_max, plim)));
+        ri.large_hi = std::max(large_lo, prime_count_le(c, plim));
+        ri.inv = inv_sum(c, large_lo, ri.large_hi);
+        ri.nsmall_large = ri.large_hi > large_lo
+                              ? std::max(large_lo, prime_count_le(c, std::min<uint64_t>(B, plim))) - large_lo
+                              : 0;
+    }
+
+    // tiles in request order; epochs cut at group boundaries
+    Plan::Epoch ep{};
+    uint64_t ep_pool = 0;
+    auto close_epoch = [&]() {
+        if (ep.ntiles == 0) return;
+        P->epochs.push_back(ep);
+        P->pool_entries = std::max(P->pool_entries, ep_pool);
+        P->max_epoch_tiles = std::max(P->max_epoch_tiles, ep.ntiles);
+        ep = Plan::Epoch{};
+        ep.tile0 = (uint32_t)P->tiles.size();
+        ep.g0 = (uint32_t)P->groups.size();
+        ep_pool = 0;
+    };
+    ep.tile0 = 0;
+    ep.g0 = 0;
+    GroupDesc grp{};
+    bool grp_open = false;
+    auto close_group = [&]() {
+        if (!grp_open) return;
+        P->groups.push_back(grp);
+        ep.ng++;
+        const uint32_t nch = (grp.p_hi - grp.p_lo + kScatterChunk - 1) / kScatterChunk;
+        ep.nchunks = std::max(ep.nchunks, nch);
+        grp_open = false;
+    };
+
+    for (size_t r = 0; r < reqs.size(); ++r) {
+        const ReqSpec &q = reqs[r];
+        const ReqInfo &ri = info[r];
+        const bool large = ri.large_hi > large_lo;
+        const uint64_t ntile = (q.nbits + B - 1) / B;
+        P->bits += q.nbits;
+        for (uint64_t k = 0; k < ntile; ++k) {
+            TileDesc d{};
+            d.J = q.j0 + k * B;
+            d.len = (uint32_t)std::min<uint64_t>(B, q.nbits - k * B);
+            d.out_word = q.out_word + (k * B) / 32;
+            d.req = q.idx;
+            d.med_hi = ri.med_hi;
+            uint32_t cap = 0;
+            if (large) {
+                const double e = (double)d.len * (8.0 / 15.0) * ri.inv;
+                cap = (uint32_t)std::ceil(1.05 * e + 8.0 * std::sqrt(e) + 64.0) + ri.nsmall_large;
+                cap = (cap + 3) & ~3u;
+            }
+            // a new scatter group when the current one is full or this tile has no
+            // large primes; a new epoch when the tile count or the pool is exhausted
+            const bool new_group = !grp_open || !large || grp.ntiles >= t.window_tiles;
+            const bool over = ep.ntiles >= t.epoch_tiles || ep_pool + cap > pool_cap;
+            if (new_group || over) close_group();
+            if (over) close_epoch();
+            d.bkt_cap = cap;
+            d.bkt_off = ep_pool;
+            ep_pool += cap;
+            const uint32_t tile_in_ep = (uint32_t)P->tiles.size() - ep.tile0;
+            P->tiles.push_back(d);
+            ep.ntiles++;
+            if (large) {
+                if (!grp_open) {
+                    grp = GroupDesc{};
+                    grp.su0 = (uint32_t)P->sus.size();
+                    grp.tile0 = tile_in_ep;
+                    grp.p_lo = large_lo;
+                    grp.p_hi = large_lo;
+                    grp_open = true;
+                }
+                // extend the group's current unit or open a new one
+                const uint32_t rel = tile_in_ep - grp.tile0;
+                bool extend = grp.nsu > 0;
+                if (extend) {
+                    SUDesc &u = P->sus.back();
+                    extend = (u.J + u.span == d.J) && u.plimit == ri.plimit;
+                    if (extend) u.span += d.len;
+                }
+                if (!extend) {
+                    SUDesc u{};
+                    u.J = d.J;
+                    u.span = d.len;
+                    u.tile_rel = rel;
+                    u.plimit = ri.plimit;
+                    P->sus.push_back(u);
+                    grp.nsu++;
+                }
+                grp.ntiles = rel + 1;
+                grp.p_hi = std::max(grp.p_hi, ri.large_hi);
+                P->exp_large_hits += (double)d.len * (8.0 / 15.0) * ri.inv;
+            }
+        }
+    }
+    close_group();
+    close_epoch();
+    if (P->pool_entries > pool_cap) P->pool_entries = pool_cap;
+    for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
+    return P;
+}
+
+}  // namespace gbs
+
+// ---------------------------------------------------------------------------
+// executor
+// ---------------------------------------------------------------------------
+namespace gbs {
+
+Plan::~Plan()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (d_tiles) cudaFree(d_tiles);
+    if (d_sus) cudaFree(d_sus);
+    if (d_groups) cudaFree(d_groups);
+}
+
+template <class T>
+static sieve_status upload_vec(T **dst, const std::vector<T> &v, cudaStream_t st)
+{
+    sieve_status s = alloc_dev((void **)dst, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (s) return s;
+    if (!v.empty()) CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return SIEVE_OK;
+}
+
+sieve_status upload_plan(sieve_ctx *c, Plan *P, cudaStream_t st)
+{
+    (void)c;
+    sieve_status s = upload_vec(&P->d_tiles, P->tiles, st);
+    if (!s) s = upload_vec(&P->d_sus, P->sus, st);
+    if (!s) s = upload_vec(&P->d_groups, P->groups, st);
+    return s;
+}
+
+static void prof_mark(sieve_ctx *c, int kind, cudaStream_t st, bool begin)
+{
+    if (!c->prof) return;
+    if (begin) {
+        ProfRec r;
+        r.kind = kind;
+        cudaEventCreate(&r.a);
+        cudaEventCreate(&r.b);
+        cudaEventRecord(r.a, st);
+        c->prof_recs.push_back(r);
+    } else {
+        cudaEventRecord(c->prof_recs.back().b, st);
+    }
+}
+
+sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, unsigned long long *counts,
+                          uint32_t ncounts, cudaStream_t ls)
+{
+    const uint32_t bt = P->tune.tile_log2;
+    if (counts && ncounts) CK(cudaMemsetAsync(counts, 0, (size_t)ncounts * 8, ls));
+    const uint32_t tgrid_max = (uint32_t)(c->nsm * tile_blocks_per_sm(bt));
+    for (const Plan::Epoch &e : P->epochs) {
+        if (e.ng) {
+            CK(cudaMemsetAsync(scr.d_bkt_cnt, 0, (size_t)e.ntiles * 4, ls));
+            CK(cudaMemsetAsync(scr.d_small + 1, 0, 4, ls));
+            ScatterArgs sa;
+            sa.primes = c->d_primes;
+            sa.barrett = c->d_barrett;
+            sa.sus = P->d_sus;
+            sa.groups = P->d_groups + e.g0;
+            sa.tiles = P->d_tiles + e.tile0;
+            sa.bkt = scr.d_bkt;
+            sa.bkt_cnt = scr.d_bkt_cnt;
+            sa.ovf = scr.d_ovf;
+            sa.ovf_cnt = scr.d_small + 1;
+            sa.ovf_cap = scr.ovf_cap;
+            sa.err = scr.d_err;
+            sa.tile_log2 = bt;
+            prof_mark(c, SIEVE_K_SCATTER, ls, true);
+            CK(launch_scatter(sa, e.nchunks, e.ng, ls));
+            prof_mark(c, SIEVE_K_SCATTER, ls, false);
+            if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt, e.ntiles, scr.d_acc + 1, ls));
+        }
+        CK(cudaMemsetAsync(scr.d_small, 0, 4, ls));
+        TileArgs ta;
+        ta.tiles = P->d_tiles + e.tile0;
+        ta.ntiles = e.ntiles;
+        ta.work = scr.d_small;
+        ta.primes = c->d_primes;
+        ta.barrett = c->d_barrett;
+        ta.med_lo = P->med_lo;
+        ta.coop_hi = P->coop_hi;
+        ta.pat = c->d_pat;
+        ta.ps = P->ps;
+        ta.bkt = scr.d_bkt;
+        ta.bkt_cnt = scr.d_bkt_cnt;
+        ta.ovf = scr.d_ovf;
+        ta.ovf_cnt = scr.d_small + 1;
+        ta.ovf_cap = scr.ovf_cap;
+        ta.out = out;
+        ta.req_counts = counts;
+        ta.tile_log2 = bt;
+        prof_mark(c, SIEVE_K_TILE, ls, true);
+        CK(launch_tiles(ta, std::min<uint32_t>(e.ntiles, tgrid_max), ls));
+        prof_mark(c, SIEVE_K_TILE, ls, false);
+    }
+    if (c->prof) {
+        c->prof_acc.tiles += P->tiles.size();
+        c->prof_acc.bits += P->bits;
+        for (const auto &g : P->groups) c->prof_acc.prime_reads += (uint64_t)(g.p_hi - g.p_lo) * g.nsu;
+    }
+    return SIEVE_OK;
+}
+
+sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long *counts, uint32_t ncounts,
+                        cudaStream_t st, bool allow_graph)
+{
+    sieve_status s = scratch_ensure(c->scr, P->pool_entries, P->max_epoch_tiles);
+    if (s) return s;
+    if (!P->d_tiles) {
+        s = upload_plan(c, P, st);
+        if (s) return s;
+    }
+    const bool graph = allow_graph && !c->prof;
+    if (graph && P->exec && P->g_out == out && P->g_counts == counts && P->g_gen == c->scr.gen) {
+        CK(cudaGraphLaunch(P->exec, st));
+        P->runs++;
+        return SIEVE_OK;
+    }
+    if (graph && P->runs >= 1) {
+        // second run of the same work: capture it once and replay from now on
+        if (P->exec) cudaGraphExecDestroy(P->exec), P->exec = nullptr;
+        if (P->graph) cudaGraphDestroy(P->graph), P->graph = nullptr;
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        sieve_status es = enqueue_plan(c, c->scr, P, out, counts, ncounts, c->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+        if (es) {
+            if (g) cudaGraphDestroy(g);
+            return es;
+        }
+        CK(ce);
+        P->graph = g;
+        CK(cudaGraphInstantiate(&P->exec, g, 0));
+        P->g_out = out;
+        P->g_counts = counts;
+        P->g_gen = c->scr.gen;
+        CK(cudaGraphLaunch(P->exec, st));
+        P->runs++;
+        return SIEVE_OK;
+    }
+    s = enqueue_plan(c, c->scr, P, out, counts, ncounts, st);
+    P->runs++;
+    return s;
+}
+
+sieve_status run_plan(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long *counts, cudaStream_t st,
+                      bool allow_graph)
+{
+    return run_plan_n(c, P, out, counts, 0, st, allow_graph);
+}
+
+}  // namespace gbs
+
+// ---------------------------------------------------------------------------
+// init: the base of Sec. 1.4 built on the device
+// ---------------------------------------------------------------------------
+static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
+{
+    const uint64_t limit = c->base_limit;
+    uint32_t *d_boot = nullptr, *d_cnt = nullptr;
+    uint64_t *d_boot_m = nullptr;
+    sieve_status s = alloc_dev((void **)&d_boot, 12288 * 4);
+    if (!s) s = alloc_dev((void **)&d_cnt, 16);
+    if (!s) s = alloc_dev((void **)&d_boot_m, 12288 * 8);
+    if (s) return s;
+    struct Guard {
+        std::vector<void *> p;
+        ~Guard() { for (void *x : p) cudaFree(x); }
+    } guard;
+    guard.p = {d_boot, d_cnt, d_boot_m};
+
+    CK(launch_bootstrap(d_boot, d_cnt, st));
+    uint32_t nboot = 0;
+    CK(cudaMemcpyAsync(&nboot, d_cnt, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<uint32_t> boot(nboot);
+    CK(cudaMemcpy(boot.data(), d_boot, (size_t)nboot * 4, cudaMemcpyDeviceToHost));
+
+    if (limit <= 131071) {
+        const uint64_t np = std::upper_bound(boot.begin(), boot.end(), (uint32_t)limit) - boot.begin();
+        c->nprimes = np;
+        s = alloc_dev((void **)&c->d_primes, std::max<uint64_t>(np, 1) * 4);
+        if (s) return s;
+        if (np) CK(cudaMemcpy(c->d_primes, d_boot, np * 4, cudaMemcpyDeviceToDevice));
+    } else {
+        // sieve indices 0..jmax (numbers 1..limit) with the bootstrap primes
+        CK(launch_barrett(d_boot, nboot, d_boot_m, st));
+        const uint64_t jmax = (limit - 1) / 2;
+        const uint64_t nbits = (jmax + 1 + 31) / 32 * 32;
+        uint32_t *d_tab = nullptr;
+        s = alloc_dev((void **)&d_tab, nbits / 8 + 16);
+        if (s) return s;
+        guard.p.push_back(d_tab);
+        const uint32_t bt = 20;
+        const uint64_t B = 1ull << bt;
+        std::vector<TileDesc> tiles;
+        const uint32_t med_lo = (uint32_t)(std::upper_bound(boot.begin(), boot.end(), c->pre.maxp[kMaxPresieveGroups - 1]) - boot.begin());
+        const uint32_t med_hi = (uint32_t)(std::upper_bound(boot.begin(), boot.end(), (uint32_t)isqrt_u64(limit)) - boot.begin());
+        for (uint64_t j = 0; j < nbits; j += B) {
+            TileDesc d{};
+            d.J = j;
+            d.len = (uint32_t)std::min<uint64_t>(B, nbits - j);
+            d.out_word = j / 32;
+            d.med_hi = std::max(med_lo, med_hi);
+            tiles.push_back(d);
+        }
+        TileDesc *d_tiles = nullptr;
+        s = upload_vec(&d_tiles, tiles, st);
+        if (s) return s;
+        guard.p.push_back(d_tiles);
+        TileArgs ta{};
+        ta.tiles = d_tiles;
+        ta.ntiles = (uint32_t)tiles.size();
+        ta.work = c->scr.d_small;
+        ta.primes = d_boot;
+        ta.barrett = d_boot_m;
+        ta.med_lo = med_lo;
+        ta.coop_hi = (uint32_t)(std::upper_bound(boot.begin(), boot.end(), 1u << 13) - boot.begin());
+        ta.pat = c->d_pat;
+        ta.ps.ngroups = kMaxPresieveGroups;
+        for (int g = 0; g < kMaxPresieveGroups; ++g) {
+            ta.ps.modulus[g] = c->pre.modulus[g];
+            ta.ps.word_off[g] = c->pre.word_off[g];
+        }
+        ta.ps.max_prime = c->pre.maxp[kMaxPresieveGroups - 1];
+        ta.ovf_cnt = c->scr.d_small + 1;
+        ta.out = d_tab;
+        ta.tile_log2 = bt;
+        CK(cudaMemsetAsync(c->scr.d_small, 0, 8, st));
+        CK(launch_tiles(ta, std::min<uint32_t>(ta.ntiles, (uint32_t)(c->nsm * tile_blocks_per_sm(bt))), st));
+        // compact the zero bits 1..jmax into the ascending prime list
+        const double lx = std::log((double)limit);
+        const uint64_t cap = (uint64_t)(1.25506 * (double)limit / lx) + 64;  // Rosser-Schoenfeld bound on pi(x)
+        s = alloc_dev((void **)&c->d_primes, cap * 4);
+        if (s) return s;
+        const uint64_t nwords = nbits / 32;
+        const uint32_t nblocks = (uint32_t)((nwords + 4095) / 4096);
+        uint32_t *d_bc = nullptr, *d_bo = nullptr;
+        s = alloc_dev((void **)&d_bc, (size_t)nblocks * 4);
+        if (!s) s = alloc_dev((void **)&d_bo, (size_t)nblocks * 4);
+        if (s) return s;
+        guard.p.push_back(d_bc);
+        guard.p.push_back(d_bo);
+        CK(launch_compact(d_tab, nbits, jmax, d_bc, d_bo, c->d_primes, d_cnt, st));
+        uint32_t np = 0;
+        CK(cudaMemcpyAsync(&np, d_cnt, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (np > cap) return SIEVE_ECUDA;
+        c->nprimes = np;
+    }
+    s = alloc_dev((void **)&c->d_barrett, std::max<uint64_t>(c->nprimes, 1) * 8);
+    if (s) return s;
+    if (c->nprimes) CK(launch_barrett(c->d_primes, c->nprimes, c->d_barrett, st));
+    c->h_primes.resize(c->nprimes);
+    if (c->nprimes) CK(cudaMemcpyAsync(c->h_primes.data(), c->d_primes, c->nprimes * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->h_inv_prefix.assign(c->nprimes / kInvBlock + 2, 0.0);
+    double acc = 0;
+    for (uint64_t i = 0; i < c->nprimes; ++i) {
+        if (i % kInvBlock == 0) c->h_inv_prefix[i / kInvBlock] = acc;
+        acc += 1.0 / c->h_primes[i];
+    }
+    for (uint64_t k = (c->nprimes + kInvBlock - 1) / kInvBlock; k < c->h_inv_prefix.size(); ++k) c->h_inv_prefix[k] = acc;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_budget)
+{
+    if (!out) return SIEVE_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SIEVE_EINVAL;
+    }
+    CK(cudaSetDevice(device));
+    std::unique_ptr<sieve_ctx> c(new sieve_ctx());
+    c->device = device;
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device));
+    CK(set_kernel_attributes());
+    c->max_v = max_v;
+    c->base_limit = std::min<uint64_t>(isqrt_u64(max_v), 0xFFFFFFFFull);
+    c->mem_budget = mem_budget ? mem_budget : (size_t)8 << 30;
+    build_presieve(c->pre);
+    sieve_status s = alloc_dev((void **)&c->d_pat, c->pre.words.size() * 4);
+    if (!s) s = scratch_init(c->scr, c->mem_budget / 4, 1u << 22);
+    if (s) {
+        sieve_destroy(c.release());
+        return s;
+    }
+    CK(cudaMemcpy(c->d_pat, c->pre.words.data(), c->pre.words.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMallocHost((void **)&c->h_acc, 64));
+    CK(cudaMallocHost((void **)&c->h_err, 16));
+    CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaEventCreateWithFlags(&c->ev_stage[i], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming));
+    }
+    for (uint32_t k = 0; k < SIEVE_TUNE_CLASSES; ++k) c->tune[k] = default_tuning(k);
+    s = build_base(c.get(), c->cap_stream);
+    if (s) {
+        sieve_destroy(c.release());
+        return s;
+    }
+    *out = c.release();
+    return SIEVE_OK;
+}
+
+void sieve_destroy(sieve_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    c->plans.clear();
+    for (void *p : {(void *)c->d_primes, (void *)c->d_barrett, (void *)c->d_pat, (void *)c->d_stage})
+        if (p) cudaFree(p);
+    scratch_free(c->scr);
+    if (c->h_acc) cudaFreeHost(c->h_acc);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_stage[i]) cudaEventDestroy(c->ev_stage[i]);
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    }
+    for (auto &r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete c;
+}
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+namespace gbs {
+
+// validate an absolute range; on success *vlast = its largest number
+sieve_status check_range(const sieve_ctx *c, uint64_t j0, uint64_t nbits, uint64_t *vlast)
+{
+    if (nbits == 0 || (j0 & 31) || (nbits & 31)) return SIEVE_EINVAL;
+    const unsigned __int128 jend = (unsigned __int128)j0 + nbits;
+    if (jend > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
+    const uint64_t v = (uint64_t)(2 * jend - 1);
+    if (isqrt_u64(v) > c->base_limit) return SIEVE_ERANGE;
+    *vlast = v;
+    return SIEVE_OK;
+}
+
+// the tuning for a single interval of nbits bits: the class default, with a
+// smaller tile when the interval has too few tiles to fill the GPU
+sieve_tuning tuning_for(const sieve_ctx *c, uint64_t vlast, uint64_t nbits)
+{
+    sieve_tuning t = c->tune[tune_class(vlast)];
+    while (t.tile_log2 > 14 && (nbits >> t.tile_log2) < (uint64_t)(4 * c->nsm)) {
+        t.tile_log2--;
+        if (t.coop_max > 64) t.coop_max >>= 1;
+    }
+    return t;
+}
+
+std::string tune_key(const sieve_tuning &t)
+{
+    char b[128];
+    std::snprintf(b, sizeof b, "%u/%u/%u/%u/%u/%u", t.tile_log2, t.presieve_groups, t.coop_max, t.medium_max,
+                  t.window_tiles, t.epoch_tiles);
+    return b;
+}
+
+Plan *cached_plan(sieve_ctx *c, const std::string &key, const std::vector<ReqSpec> &reqs, const sieve_tuning &t)
+{
+    auto it = c->plans.find(key);
+    if (it != c->plans.end()) return it->second.get();
+    if (c->plans.size() >= 64) {
+        cudaDeviceSynchronize();
+        c->plans.clear();
+    }
+    std::unique_ptr<Plan> P = build_plan(c, reqs, t);
+    Plan *raw = P.get();
+    c->plans[key] = std::move(P);
+    return raw;
+}
+
+}  // namespace gbs
+
+sieve_status sieve_segments(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, uint32_t *dev_bits,
+                            sieve_stream stream)
+{
+    if (!c || !dev_bits || l < 5 || l > 40 || n == 0 || ((uintptr_t)dev_bits & 3)) return SIEVE_EINVAL;
+    if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
+    const uint64_t j0 = f << l, nbits = n << l;
+    uint64_t vlast;
+    sieve_status s = check_range(c, j0, nbits, &vlast);
+    if (s) return s;
+    CK(cudaSetDevice(c->device));
+    const sieve_tuning t = tuning_for(c, vlast, nbits);
+    char key[160];
+    std::snprintf(key, sizeof key, "S/%llu/%llu/%p/", (unsigned long long)j0, (unsigned long long)nbits,
+                  (void *)dev_bits);
+    std::vector<ReqSpec> reqs{{j0, nbits, 0, 0}};
+    Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
+    return run_plan(c, P, dev_bits, nullptr, (cudaStream_t)stream, true);
+}
+
+sieve_status sieve_f_from_midpoint(uint32_t l, uint64_t n, uint64_t mant, uint32_t exp10, uint64_t *f_out)
+{
+    if (!f_out || l < 5 || l > 40) return SIEVE_EINVAL;
+    unsigned __int128 M = mant;
+    for (uint32_t i = 0; i < exp10; ++i) {
+        M *= 10;
+        if (M >> 64) return SIEVE_ERANGE;
+    }
+    const unsigned __int128 q = M >> (l + 1), h = n / 2;
+    *f_out = q > h ? (uint64_t)(q - h) : 0;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_segments_midpoint(sieve_ctx *c, uint32_t l, uint64_t mant, uint32_t exp10, uint64_t n,
+                                     uint32_t *dev_bits, sieve_stream stream)
+{
+    uint64_t f;
+    sieve_status s = sieve_f_from_midpoint(l, n, mant, exp10, &f);
+    if (s) return s;
+    return sieve_segments(c, l, f, n, dev_bits, stream);
+}
+
+static sieve_status take_device_error(sieve_ctx *c, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(c->h_err, c->scr.d_err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int e = *c->h_err;
+    if (e) {
+        CK(cudaMemsetAsync(c->scr.d_err, 0, 4, st));
+        CK(cudaStreamSynchronize(st));
+        return (e & kErrTimeout) ? SIEVE_ETIMEOUT : SIEVE_EOVERFLOW;
+    }
+    return SIEVE_OK;
+}
+
+sieve_status sieve_sync(sieve_ctx *c, sieve_stream stream)
+{
+    if (!c) return SIEVE_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaGetLastError());
+    return take_device_error(c, (cudaStream_t)stream);
+}
+
+sieve_status sieve_count(sieve_ctx *c, const uint32_t *dev_bits, uint64_t nbits, uint64_t *host_count,
+                         sieve_stream stream)
+{
+    if (!c || !host_count || (nbits & 31) || (nbits && !dev_bits)) return SIEVE_EINVAL;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->scr.d_acc, 0, 8, st));
+    if (nbits) {
+        prof_mark(c, SIEVE_K_COUNT, st, true);
+        CK(launch_popcount(dev_bits, nbits / 32, c->scr.d_acc, (uint32_t)(c->nsm * 4), st));
+        prof_mark(c, SIEVE_K_COUNT, st, false);
+    }
+    CK(cudaMemcpyAsync(c->h_acc, c->scr.d_acc, 8, cudaMemcpyDeviceToHost, st));
+    sieve_status s = take_device_error(c, st);  // synchronises the stream
+    *host_count = c->h_acc[0];
+    return s;
+}
+
+sieve_status sieve_segments_host(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, uint32_t *host_bits,
+                                 sieve_stream stream)
+{
+    if (!c || !host_bits || l < 5 || l > 40 || n == 0) return SIEVE_EINVAL;
+    if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
+    const uint64_t j0 = f << l, nbits = n << l;
+    uint64_t vlast;
+    sieve_status s = check_range(c, j0, nbits, &vlast);
+    if (s) return s;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // windows of up to 2^31 bits, double-buffered on the device: sieve window k
+    // into stage k%2 on `stream`, copy it to the host on the copy stream
+    const uint64_t C = std::min<uint64_t>(nbits, 1ull << 31);
+    s = ensure((void **)&c->d_stage, &c->stage_bytes, 2 * (C / 8) + 64, nullptr);
+    if (s) return s;
+    uint32_t *stage[2] = {c->d_stage, c->d_stage + C / 32};
+    const sieve_tuning t = tuning_for(c, vlast, C);
+    const uint64_t nwin = (nbits + C - 1) / C;
+    for (uint64_t k = 0; k < nwin; ++k) {
+        const uint64_t wj = j0 + k * C, wn = std::min<uint64_t>(C, nbits - k * C);
+        const int b = (int)(k & 1);
+        if (k >= 2) CK(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
+        char key[160];
+        std::snprintf(key, sizeof key, "H/%llu/%llu/%p/", (unsigned long long)wj, (unsigned long long)wn,
+                      (void *)stage[b]);
+        std::vector<ReqSpec> reqs{{wj, wn, 0, 0}};
+        Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
+        s = run_plan(c, P, stage[b], nullptr, st, true);
+        if (s) return s;
+        CK(cudaEventRecord(c->ev_stage[b], st));
+        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_stage[b], 0));
+        prof_mark(c, SIEVE_K_COPY, c->copy_stream, true);
+        CK(cudaMemcpyAsync(host_bits + (k * C) / 32, stage[b], wn / 8, cudaMemcpyDeviceToHost, c->copy_stream));
+        prof_mark(c, SIEVE_K_COPY, c->copy_stream, false);
+        CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+    }
+    CK(cudaStreamSynchronize(c->copy_stream));
+    return sieve_sync(c, stream);
+}
+
+sieve_status sieve_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t count, uint32_t *dev_arena,
+                         uint64_t *dev_counts, sieve_stream stream)
+{
+    if (!c || (count && (!reqs || !dev_arena || !dev_counts)) || ((uintptr_t)dev_arena & 3)) return SIEVE_EINVAL;
+    if (count == 0) return SIEVE_OK;
+    CK(cudaSetDevice(c->device));
+    std::vector<ReqSpec> rs(count);
+    std::vector<uint64_t> vl(count);
+    uint64_t vmax = 0, total = 0;
+    // key: the request list and the output pointers
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t x) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (x >> (8 * i)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    for (uint32_t r = 0; r < count; ++r) {
+        sieve_status s = check_range(c, reqs[r].j0, reqs[r].nbits, &vl[r]);
+        if (s) return s;
+        rs[r] = ReqSpec{reqs[r].j0, reqs[r].nbits, reqs[r].out_word_off, r};
+        vmax = std::max(vmax, vl[r]);
+        total += reqs[r].nbits;
+        mix(reqs[r].j0);
+        mix(reqs[r].nbits);
+        mix(reqs[r].out_word_off);
+    }
+    // largest magnitudes first: the heaviest tiles start first, and requests of
+    // similar magnitude share scatter groups
+    std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
+    sieve_tuning t = c->batch_tune.tile_log2 ? c->batch_tune : c->tune[tune_class(vmax)];
+    char key[200];
+    std::snprintf(key, sizeof key, "B/%u/%016llx/%p/%p/", count, (unsigned long long)h, (void *)dev_arena,
+                  (void *)dev_counts);
+    Plan *P = cached_plan(c, std::string(key) + tune_key(t), rs, t);
+    (void)total;
+    return run_plan_n(c, P, dev_arena, (unsigned long long *)dev_counts, count, (cudaStream_t)stream, true);
+}
+
+sieve_status sieve_get_tuning(sieve_ctx *c, uint32_t cls, sieve_tuning *out)
+{
+    if (!c || !out || cls >= SIEVE_TUNE_CLASSES) return SIEVE_EINVAL;
+    *out = c->tune[cls];
+    return SIEVE_OK;
+}
+
+sieve_status sieve_set_tuning(sieve_ctx *c, uint32_t cls, const sieve_tuning *in)
+{
+    if (!c || !in || cls >= SIEVE_TUNE_CLASSES || !tuning_valid(*in)) return SIEVE_EINVAL;
+    c->tune[cls] = *in;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_base_info(sieve_ctx *c, const uint32_t **dev_primes, uint64_t *count, uint64_t *limit)
+{
+    if (!c) return SIEVE_EINVAL;
+    if (dev_primes) *dev_primes = c->d_primes;
+    if (count) *count = c->nprimes;
+    if (limit) *limit = c->base_limit;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_profile_enable(sieve_ctx *c, int enable)
+{
+    if (!c) return SIEVE_EINVAL;
+    c->prof = enable != 0;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_profile_read(sieve_ctx *c, sieve_profile *out, sieve_stream stream)
+{
+    if (!c || !out) return SIEVE_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaStreamSynchronize(c->copy_stream));
+    for (auto &r : c->prof_recs) {
+        float ms = 0;
+        CK(cudaEventSynchronize(r.b));
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (r.kind >= 0 && r.kind < 8) {
+            c->prof_acc.launches[r.kind]++;
+            c->prof_acc.ms[r.kind] += ms;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->prof_recs.clear();
+    CK(cudaMemcpy(c->h_acc, c->scr.d_acc, 16, cudaMemcpyDeviceToHost));
+    c->prof_acc.large_hits = c->h_acc[1];
+    *out = c->prof_acc;
+    c->prof_acc = sieve_profile{};
+    CK(cudaMemset(c->scr.d_acc + 1, 0, 8));
+    return SIEVE_OK;
+}
+
+sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s)
+{
+    if (!atomics_per_s) return SIEVE_EINVAL;
+    CK(cudaSetDevice(device));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    CK(probe_smem_atomics(nsm, atomics_per_s));
+    return SIEVE_OK;
+}

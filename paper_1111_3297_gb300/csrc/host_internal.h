@@ -1,0 +1,138 @@
+// Host-side internals shared by the C ABI translation units (context, plans).
+#pragma once
+#include "gbsieve.h"
+#include "sieve_internal.cuh"
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+namespace gbs {
+
+constexpr uint32_t kInvBlock = 256;  // granularity of the 1/p prefix table
+
+struct PresieveTable {
+    std::vector<uint32_t> words;
+    uint32_t modulus[kMaxPresieveGroups];
+    uint32_t word_off[kMaxPresieveGroups];
+    uint32_t maxp[kMaxPresieveGroups];
+};
+void build_presieve(PresieveTable &t);
+
+struct ReqSpec {
+    uint64_t j0, nbits, out_word;
+    uint32_t idx;
+};
+
+struct Plan {
+    sieve_tuning tune;
+    PresieveInfo ps;
+    uint32_t med_lo = 0, coop_hi = 0;
+    std::vector<TileDesc> tiles;
+    std::vector<SUDesc> sus;
+    std::vector<GroupDesc> groups;
+    struct Epoch {
+        uint32_t tile0, ntiles;  // tiles [tile0, tile0+ntiles)
+        uint32_t g0, ng;         // scatter groups [g0, g0+ng)
+        uint32_t nchunks;        // scatter grid x
+    };
+    std::vector<Epoch> epochs;
+    uint64_t pool_entries = 0;
+    uint32_t max_epoch_tiles = 0;
+    uint64_t bits = 0;
+    double exp_large_hits = 0;
+    // device copies of the descriptors
+    TileDesc *d_tiles = nullptr;
+    SUDesc *d_sus = nullptr;
+    GroupDesc *d_groups = nullptr;
+    // graph replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t *g_out = nullptr;
+    unsigned long long *g_counts = nullptr;
+    uint64_t g_gen = 0;
+    uint32_t runs = 0;
+    ~Plan();
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+// device scratch of one launch sequence in flight (the context owns one; each
+// serving lane owns its own so that batches on different streams never share)
+struct Scratch {
+    uint32_t *d_bkt = nullptr;  // large-prime bucket pool
+    size_t bkt_bytes = 0;
+    uint32_t *d_bkt_cnt = nullptr;  // entries per tile of the current epoch
+    size_t bkt_cnt_bytes = 0;
+    unsigned long long *d_ovf = nullptr;  // overflow backstop list
+    uint32_t ovf_cap = 0;
+    uint32_t *d_small = nullptr;  // [0] tile work counter, [1] overflow count
+    int *d_err = nullptr;         // device error bits
+    unsigned long long *d_acc = nullptr;  // [0] popcount, [1] profiled hits
+    uint64_t gen = 0;             // bumped when a buffer moves (captured graphs re-capture)
+    uint64_t pool_entries = 0;    // bucket pool capacity allowed (entries)
+};
+sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap);
+void scratch_free(Scratch &s);
+sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles);
+}  // namespace gbs
+
+struct sieve_ctx {
+    int device = 0;
+    int nsm = 0;
+    uint64_t max_v = 0, base_limit = 0, nprimes = 0;
+    uint32_t *d_primes = nullptr;
+    uint64_t *d_barrett = nullptr;
+    std::vector<uint32_t> h_primes;
+    std::vector<double> h_inv_prefix;  // sum of 1/p over the first k*kInvBlock primes
+    gbs::PresieveTable pre;
+    uint32_t *d_pat = nullptr;
+    sieve_tuning tune[SIEVE_TUNE_CLASSES];
+    size_t mem_budget = 0;
+    gbs::Scratch scr;
+    unsigned long long *h_acc = nullptr;  // pinned
+    int *h_err = nullptr;                 // pinned
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    sieve_tuning batch_tune{};   // autotuned tuning for batches (tile_log2 == 0: class default)
+    // staging for the host-output path
+    uint32_t *d_stage = nullptr;
+    size_t stage_bytes = 0;
+    // plans
+    std::map<std::string, std::unique_ptr<gbs::Plan>> plans;
+    // profiling
+    bool prof = false;
+    std::vector<gbs::ProfRec> prof_recs;
+    sieve_profile prof_acc{};
+    int sticky_err = 0;
+};
+
+namespace gbs {
+extern char g_last_cuda_error[512];
+uint64_t isqrt_u64(uint64_t x);
+uint32_t prime_count_le(const sieve_ctx *c, uint64_t x);
+double inv_sum(const sieve_ctx *c, uint32_t a, uint32_t b);
+uint32_t tune_class(uint64_t vlast);
+sieve_tuning default_tuning(uint32_t cls);
+bool tuning_valid(const sieve_tuning &t);
+std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tuning t,
+                                 uint64_t pool_cap = 0);
+sieve_status check_range(const sieve_ctx *c, uint64_t j0, uint64_t nbits, uint64_t *vlast);
+sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, unsigned long long *counts,
+                          uint32_t ncounts, cudaStream_t ls);
+sieve_status run_plan(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long *counts, cudaStream_t st,
+                      bool allow_graph);
+sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long *counts, uint32_t ncounts,
+                        cudaStream_t st, bool allow_graph);
+sieve_tuning tuning_for(const sieve_ctx *c, uint64_t vlast, uint64_t nbits);
+std::string tune_key(const sieve_tuning &t);
+Plan *cached_plan(sieve_ctx *c, const std::string &key, const std::vector<ReqSpec> &reqs, const sieve_tuning &t);
+sieve_status upload_plan(sieve_ctx *c, Plan *P, cudaStream_t st);
+}  // namespace gbs

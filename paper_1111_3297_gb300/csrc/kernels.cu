@@ -1,0 +1,693 @@
+// Device kernels of the GB300 sieve (sm_103a).
+//
+//   k_tile       one on-chip segment ("tile", Sec. 1.3 segments) per CTA, persistent
+//                grid: pre-sieve by pattern copy (Sec. 3.1), medium primes striding
+//                through shared memory with the mod-15 wheel (Sec. 2.1, Sec. 3.2.1),
+//                drain of the tile's large-prime bucket (Sec. 2.2-2.3), coalesced
+//                128-bit store and popcount.
+//   k_scatter    large primes (stride beyond the tile): first hit by Barrett reduction
+//                (Lemma lem:q, Sec. 1.4), all hits of a window staged in shared memory
+//                per warp, counting-sorted by tile and appended to per-tile buckets in
+//                HBM with one atomic reservation per (tile, flush).
+//   k_bootstrap, k_compact_*, k_barrett   the base of Sec. 1.4 built on the device.
+//   k_popcount   composite count of a table.
+//   k_probe_smem shared-memory atomic-OR rate (roofline denominator).
+#include "sieve_internal.cuh"
+
+namespace gbs {
+
+__constant__ uint32_t c_cum[8] = {pack_cum(0), pack_cum(1), pack_cum(2), pack_cum(3),
+                                  pack_cum(4), pack_cum(5), pack_cum(6), pack_cum(7)};
+
+// bit (q-1)/2 set for every odd prime q <= 127: a pre-sieve pattern marks q*1 = q
+// itself, which is prime, so those bits are cleared again where they occur
+constexpr uint64_t small_prime_bits()
+{
+    uint64_t x = 0;
+    for (int q = 3; q <= 127; q += 2) {
+        bool pr = true;
+        for (int d = 3; d * d <= q; d += 2)
+            if (q % d == 0) pr = false;
+        if (pr) x |= 1ull << ((q - 1) / 2);
+    }
+    return x;
+}
+constexpr uint64_t kSmallPrimeBits = small_prime_bits();
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// tile kernel
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(T) k_tile(TileArgs a)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_rho0[kMaxPresieveGroups];
+    __shared__ uint32_t s_red[T / 32];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t ng = a.ps.ngroups;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(a.work, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= a.ntiles) break;
+        const TileDesc d = a.tiles[t];
+        const uint32_t len = d.len, nwords = len >> 5;
+
+        // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
+        if (tid < ng) s_rho0[tid] = (uint32_t)(d.J % a.ps.modulus[tid]);
+        __syncthreads();
+        {
+            uint32_t rho[kMaxPresieveGroups], inc[kMaxPresieveGroups];
+#pragma unroll
+            for (int g = 0; g < kMaxPresieveGroups; ++g) {
+                if (g < (int)ng) {
+                    const uint32_t P = a.ps.modulus[g];
+                    rho[g] = (s_rho0[g] + 32u * tid) % P;
+                    inc[g] = (32u * T) % P;
+                } else {
+                    rho[g] = 0;
+                    inc[g] = 0;
+                }
+            }
+            for (uint32_t w = tid; w < nwords; w += T) {
+                uint32_t mask = 0;
+#pragma unroll
+                for (int g = 0; g < kMaxPresieveGroups; ++g) {
+                    if (g < (int)ng) {
+                        const uint32_t *pt = a.pat + a.ps.word_off[g];
+                        const uint32_t r = rho[g];
+                        const uint32_t lo = __ldg(pt + (r >> 5)), hi = __ldg(pt + (r >> 5) + 1);
+                        mask |= __funnelshift_r(lo, hi, r & 31);
+                        uint32_t nr = r + inc[g];
+                        rho[g] = nr >= a.ps.modulus[g] ? nr - a.ps.modulus[g] : nr;
+                    }
+                }
+                const uint64_t Jw = d.J + 32ull * w;
+                if (Jw < 64) mask &= ~(uint32_t)(kSmallPrimeBits >> Jw);
+                sm[w] = mask;
+            }
+        }
+        __syncthreads();
+
+        // ---- medium primes (Sec. 2.1, Sec. 3.2), wheel of Sec. 3.2.1 ----
+        const uint32_t js15 = (uint32_t)(d.J % 15u);
+        const uint32_t coop_end = min(a.coop_hi, d.med_hi);
+        {
+            // warp-cooperative: one prime per warp at a time, lane i strikes the
+            // (i%8)-th admissible multiple of wheel period i/8; 60 steps of p per pass
+            const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
+            for (uint32_t b = a.med_lo + warp * 32u; b < coop_end; b += T) {
+                const uint32_t idx = b + lane;
+                uint32_t p = 0, h = len, s = 0;
+                if (idx < coop_end) {
+                    p = a.primes[idx];
+                    const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
+                    h = hh < len ? (uint32_t)hh : len;
+                }
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
+                    const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
+                    const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
+                    if (hj >= len) continue;
+                    const uint32_t k = lane_base + ((c_cum[sj] >> cum_shift) & 15u);
+                    uint32_t pos = hj + k * pj;
+                    const uint32_t step = 60u * pj;
+                    while (pos < len) {
+                        atomicOr(&sm[pos >> 5], 1u << (pos & 31));
+                        pos += step;
+                    }
+                }
+            }
+        }
+        {
+            // one prime per thread
+            for (uint32_t idx = max(a.med_lo, a.coop_hi) + tid; idx < d.med_hi; idx += T) {
+                const uint32_t p = a.primes[idx];
+                uint32_t s;
+                const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
+                if (hh >= len) continue;
+                uint32_t h = (uint32_t)hh;
+                for (;;) {
+                    atomicOr(&sm[h >> 5], 1u << (h & 31));
+                    h += wheel_gap(s) * p;  // medium primes < 2^28: no overflow
+                    s = (s + 1) & 7;
+                    if (h >= len) break;
+                }
+            }
+        }
+
+        // ---- drain the tile's large-prime bucket (Sec. 2.2-2.3) ----
+        if (d.bkt_cap) {
+            const uint32_t cnt = min(a.bkt_cnt[t], d.bkt_cap);
+            const uint32_t *e = a.bkt + d.bkt_off;
+            const uint32_t n4 = cnt >> 2;
+            const uint4 *e4 = reinterpret_cast<const uint4 *>(e);
+            for (uint32_t i = tid; i < n4; i += T) {
+                const uint4 v = __ldcs(e4 + i);
+                atomicOr(&sm[v.x >> 5], 1u << (v.x & 31));
+                atomicOr(&sm[v.y >> 5], 1u << (v.y & 31));
+                atomicOr(&sm[v.z >> 5], 1u << (v.z & 31));
+                atomicOr(&sm[v.w >> 5], 1u << (v.w & 31));
+            }
+            for (uint32_t i = 4 * n4 + tid; i < cnt; i += T) {
+                const uint32_t v = __ldcs(e + i);
+                atomicOr(&sm[v >> 5], 1u << (v & 31));
+            }
+            const uint32_t oc = min(*(volatile const uint32_t *)a.ovf_cnt, a.ovf_cap);
+            for (uint32_t i = tid; i < oc; i += T) {
+                const unsigned long long x = a.ovf[i];
+                if ((uint32_t)(x >> 32) == t) {
+                    const uint32_t v = (uint32_t)x;
+                    atomicOr(&sm[v >> 5], 1u << (v & 31));
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- store (128-bit when aligned) and popcount ----
+        uint32_t pop = 0;
+        uint32_t *out = a.out + d.out_word;
+        if (((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((nwords & 3) == 0)) {
+            uint4 *o4 = reinterpret_cast<uint4 *>(out);
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(sm);
+            for (uint32_t i = tid; i < (nwords >> 2); i += T) {
+                const uint4 v = s4[i];
+                o4[i] = v;
+                pop += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        } else {
+            for (uint32_t i = tid; i < nwords; i += T) {
+                const uint32_t v = sm[i];
+                out[i] = v;
+                pop += __popc(v);
+            }
+        }
+        if (a.req_counts) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
+            if (lane == 0) s_red[warp] = pop;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t v = lane < T / 32 ? s_red[lane] : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) atomicAdd(&a.req_counts[d.req], (unsigned long long)v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int tile_threads(uint32_t tile_log2) { return tile_log2 >= 17 ? 1024 : (tile_log2 >= 14 ? 512 : 256); }
+size_t tile_smem_bytes(uint32_t tile_log2) { return (size_t)1 << (tile_log2 - 3); }
+
+template <int T>
+static cudaError_t launch_tiles_t(const TileArgs &a, uint32_t grid, cudaStream_t st)
+{
+    const size_t smem = tile_smem_bytes(a.tile_log2);
+    k_tile<T><<<grid, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st)
+{
+    switch (tile_threads(a.tile_log2)) {
+    case 1024: return launch_tiles_t<1024>(a, grid, st);
+    case 512: return launch_tiles_t<512>(a, grid, st);
+    default: return launch_tiles_t<256>(a, grid, st);
+    }
+}
+
+int tile_blocks_per_sm(uint32_t tile_log2)
+{
+    int n = 0;
+    const size_t smem = tile_smem_bytes(tile_log2);
+    switch (tile_threads(tile_log2)) {
+    case 1024:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<1024>, 1024, smem);
+        break;
+    case 512:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<512>, 512, smem);
+        break;
+    default:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile<256>, 256, smem);
+    }
+    return n < 1 ? 1 : n;
+}
+
+// ---------------------------------------------------------------------------
+// scatter kernel: large primes -> per-tile buckets
+//
+// CTA (chunk, group): up to kScatterChunk consecutive large primes, one scatter
+// group (<= kScatterMaxTiles tiles of one or more requests).  Prime-major: a warp
+// takes 32 primes (one per lane, prime and Barrett constant in registers), walks
+// the group's scatter units, computes each unit's first hit (Lemma lem:q, the p^2
+// start of Sec. 1.4, the wheel of Sec. 3.2.1) and emits every hit of the unit
+// into its own staging buffer in shared memory.  When a warp's buffer is full
+// the CTA flushes: histogram by tile, one atomic reservation per (tile, flush) in
+// the tile's bucket, counting sort in shared memory, and a store pass in which
+// consecutive lanes write consecutive bucket slots.  Entries are the hit's bit
+// offset inside its tile (uint32).  A bucket that would overflow its capacity
+// spills to a global backstop list instead.
+// ---------------------------------------------------------------------------
+constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 1024, kScE = kScNW * kScEW;
+constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
+                           (size_t)kScatterMaxTiles * (4 + 4 + 8 + 8) /*hist,start,gb,lim*/;
+
+__global__ void __launch_bounds__(kScT, 1) k_scatter(ScatterArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long *gb = reinterpret_cast<unsigned long long *>(smraw);
+    unsigned long long *lim = gb + kScatterMaxTiles;
+    uint32_t *buf = reinterpret_cast<uint32_t *>(lim + kScatterMaxTiles);
+    uint32_t *srt = buf + kScE;
+    uint32_t *hist = srt + kScE;
+    uint32_t *start = hist + kScatterMaxTiles;
+    __shared__ uint32_t wc[kScNW];
+    __shared__ uint32_t s_total;
+
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const GroupDesc g = a.groups[blockIdx.y];
+    const uint32_t lo = g.p_lo + blockIdx.x * kScatterChunk;
+    if (lo >= g.p_hi) return;
+    const uint32_t n = min(kScatterChunk, g.p_hi - lo);
+    const uint32_t nlg = (n + 31) / 32;
+    const uint32_t bt = a.tile_log2, Bm = (1u << bt) - 1;
+    const uint32_t su_end = g.su0 + g.nsu;
+
+    uint32_t lg = warp, su = g.su0;
+    bool need_load = true, need_hit = true;
+    uint32_t p = 0, h = kStateInf, s = 0;
+    uint64_t m = 0;
+    uint32_t *wb = buf + warp * kScEW;
+
+    for (;;) {
+        // ---- generate into the warp's staging buffer ----
+        uint32_t wcnt = 0;
+        bool full = false;
+        while (lg < nlg) {
+            if (need_load) {
+                const uint32_t idx = lg * 32 + lane;
+                p = idx < n ? a.primes[lo + idx] : 0u;
+                m = idx < n ? a.barrett[lo + idx] : 0ull;
+                need_load = false;
+            }
+            const SUDesc u = a.sus[su];
+            if (need_hit) {
+                h = kStateInf;
+                s = 0;
+                if (p != 0 && p <= u.plimit) {
+                    const uint64_t hh = first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
+                    if (hh < kStateInf) h = (uint32_t)hh;
+                }
+                need_hit = false;
+            }
+            const uint32_t ebase = u.tile_rel << bt;
+            for (;;) {
+                const bool act = h < u.span;
+                const uint32_t mask = __ballot_sync(0xffffffffu, act);
+                if (!mask) break;
+                if (wcnt + 32 > (uint32_t)kScEW) {
+                    full = true;
+                    break;
+                }
+                if (act) {
+                    wb[wcnt + __popc(mask & lanemask_lt())] = ebase + h;
+                    const uint64_t nh = (uint64_t)h + (uint64_t)wheel_gap(s) * p;
+                    h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
+                    s = (s + 1) & 7;
+                }
+                wcnt += __popc(mask);
+            }
+            if (full) break;
+            need_hit = true;
+            if (++su == su_end) {
+                su = g.su0;
+                lg += kScNW;
+                need_load = true;
+            }
+        }
+        if (lane == 0) wc[warp] = wcnt;
+        const bool more = lg < nlg;
+        for (uint32_t k = tid; k < g.ntiles; k += kScT) hist[k] = 0;
+        __syncthreads();
+
+        // ---- flush: histogram by tile ----
+        for (uint32_t e = tid; e < (uint32_t)kScE; e += kScT) {
+            if ((e % kScEW) < wc[e / kScEW]) atomicAdd(&hist[buf[e] >> bt], 1u);
+        }
+        __syncthreads();
+        // ---- exclusive scan (one warp) ----
+        if (warp == 0) {
+            const uint32_t per = (g.ntiles + 31) / 32;
+            const uint32_t base = lane * per;
+            uint32_t sum = 0;
+            for (uint32_t j = 0; j < per; ++j)
+                if (base + j < g.ntiles) sum += hist[base + j];
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            uint32_t run = incl - sum;
+            for (uint32_t j = 0; j < per; ++j) {
+                if (base + j < g.ntiles) {
+                    start[base + j] = run;
+                    run += hist[base + j];
+                }
+            }
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+        // ---- one reservation per non-empty tile ----
+        for (uint32_t k = tid; k < g.ntiles; k += kScT) {
+            const uint32_t c = hist[k];
+            if (c) {
+                const TileDesc &td = a.tiles[g.tile0 + k];
+                gb[k] = td.bkt_off + atomicAdd(&a.bkt_cnt[g.tile0 + k], c);
+                lim[k] = td.bkt_off + td.bkt_cap;
+            }
+            hist[k] = start[k];
+        }
+        __syncthreads();
+        // ---- counting sort into srt ----
+        for (uint32_t e = tid; e < (uint32_t)kScE; e += kScT) {
+            if ((e % kScEW) < wc[e / kScEW]) {
+                const uint32_t v = buf[e];
+                srt[atomicAdd(&hist[v >> bt], 1u)] = v;
+            }
+        }
+        __syncthreads();
+        // ---- store: consecutive lanes -> consecutive slots of one bucket ----
+        const uint32_t total = s_total;
+        for (uint32_t i = tid; i < total; i += kScT) {
+            const uint32_t v = srt[i];
+            const uint32_t k = v >> bt;
+            const unsigned long long dst = gb[k] + (i - start[k]);
+            const uint32_t off = v & Bm;
+            if (dst < lim[k]) {
+                a.bkt[dst] = off;
+            } else {
+                const uint32_t o = atomicAdd(a.ovf_cnt, 1u);
+                if (o < a.ovf_cap)
+                    a.ovf[o] = ((unsigned long long)(g.tile0 + k) << 32) | off;
+                else
+                    atomicOr(a.err, kErrOverflow);
+            }
+        }
+        if (!__syncthreads_or(more)) break;
+    }
+}
+
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, uint32_t ngroups, cudaStream_t st)
+{
+    k_scatter<<<dim3(nchunks, ngroups), kScT, kScSmem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// base of Sec. 1.4 on the device
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of one value per thread (T threads); returns the
+// exclusive prefix, total in *tot
+template <int T>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *tot)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < T / 32 ? s_warp[lane] : 0;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (uint32_t)o) wi += y;
+        }
+        if (lane < T / 32) s_warp[lane] = wi - w;
+        if (lane == T / 32 - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + incl - v;
+    *tot = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+// odd primes below 2^17 (index j < 2^16 stands for 2j+1), one CTA: striking with
+// every odd d <= 361 = floor(sqrt(131071)) from d^2 on (Sec. 1.1, Sec. 1.4)
+__global__ void __launch_bounds__(1024) k_bootstrap(uint32_t *primes_out, uint32_t *count_out)
+{
+    __shared__ uint32_t bits[2048];
+    __shared__ uint32_t s_warp[33];
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < 2048; i += 1024) bits[i] = 0;
+    __syncthreads();
+    if (tid < 180) {
+        const uint32_t d = 2 * tid + 3;
+        for (uint32_t j = (d * d - 1) / 2; j < 65536; j += d) atomicOr(&bits[j >> 5], 1u << (j & 31));
+    }
+    __syncthreads();
+    uint32_t w0 = ~bits[2 * tid], w1 = ~bits[2 * tid + 1];
+    if (tid == 0) w0 &= ~1u;  // the number 1
+    uint32_t tot;
+    uint32_t pos = block_excl_scan<1024>(__popc(w0) + __popc(w1), s_warp, &tot);
+    while (w0) {
+        const uint32_t b = __ffs(w0) - 1;
+        w0 &= w0 - 1;
+        primes_out[pos++] = 2 * (64 * tid + b) + 1;
+    }
+    while (w1) {
+        const uint32_t b = __ffs(w1) - 1;
+        w1 &= w1 - 1;
+        primes_out[pos++] = 2 * (64 * tid + 32 + b) + 1;
+    }
+    if (tid == 0) *count_out = tot;
+}
+
+constexpr int kCpT = 1024, kCpW = 4;  // compaction: threads per block, words per thread
+
+// zero bits of word w among valid indices 1..jmax
+__device__ __forceinline__ uint32_t prime_bits(const uint32_t *bits, uint64_t w, uint64_t nwords,
+                                               uint64_t jmax)
+{
+    if (w >= nwords) return 0;
+    uint32_t v = ~bits[w];
+    if (w == 0) v &= ~1u;
+    const uint64_t j = 32 * w;
+    if (j > jmax) return 0;
+    if (jmax - j < 31) v &= (1u << (jmax - j + 1)) - 1;
+    return v;
+}
+
+__global__ void __launch_bounds__(kCpT) k_compact_count(const uint32_t *bits, uint64_t nwords, uint64_t jmax,
+                                                        uint32_t *block_cnt)
+{
+    __shared__ uint32_t s_warp[33];
+    const uint64_t w0 = ((uint64_t)blockIdx.x * kCpT + threadIdx.x) * kCpW;
+    uint32_t c = 0;
+    for (int k = 0; k < kCpW; ++k) c += __popc(prime_bits(bits, w0 + k, nwords, jmax));
+    uint32_t tot;
+    block_excl_scan<kCpT>(c, s_warp, &tot);
+    if (threadIdx.x == 0) block_cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_compact_scan(const uint32_t *block_cnt, uint32_t nblocks,
+                                                       uint32_t *block_off, uint32_t *total)
+{
+    __shared__ uint32_t s_warp[33];
+    const uint32_t per = (nblocks + 1023) / 1024;
+    const uint32_t base = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (uint32_t k = 0; k < per; ++k)
+        if (base + k < nblocks) sum += block_cnt[base + k];
+    uint32_t tot;
+    uint32_t run = block_excl_scan<1024>(sum, s_warp, &tot);
+    for (uint32_t k = 0; k < per; ++k) {
+        if (base + k < nblocks) {
+            block_off[base + k] = run;
+            run += block_cnt[base + k];
+        }
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void __launch_bounds__(kCpT) k_compact_write(const uint32_t *bits, uint64_t nwords, uint64_t jmax,
+                                                        const uint32_t *block_off, uint32_t *primes_out)
+{
+    __shared__ uint32_t s_warp[33];
+    const uint64_t w0 = ((uint64_t)blockIdx.x * kCpT + threadIdx.x) * kCpW;
+    uint32_t v[kCpW];
+    uint32_t c = 0;
+    for (int k = 0; k < kCpW; ++k) {
+        v[k] = prime_bits(bits, w0 + k, nwords, jmax);
+        c += __popc(v[k]);
+    }
+    uint32_t tot;
+    uint32_t pos = block_off[blockIdx.x] + block_excl_scan<kCpT>(c, s_warp, &tot);
+    for (int k = 0; k < kCpW; ++k) {
+        uint32_t x = v[k];
+        while (x) {
+            const uint32_t b = __ffs(x) - 1;
+            x &= x - 1;
+            primes_out[pos++] = (uint32_t)(2 * (32 * (w0 + k) + b) + 1);
+        }
+    }
+}
+
+cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st)
+{
+    k_bootstrap<<<1, 1024, 0, st>>>(primes_out, count_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
+                           uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out, cudaStream_t st)
+{
+    const uint64_t nwords = nbits / 32;
+    const uint32_t nblocks = (uint32_t)((nwords + (uint64_t)kCpT * kCpW - 1) / ((uint64_t)kCpT * kCpW));
+    k_compact_count<<<nblocks, kCpT, 0, st>>>(bits, nwords, jmax, block_cnt);
+    k_compact_scan<<<1, 1024, 0, st>>>(block_cnt, nblocks, block_off, total_out);
+    if (primes_out) k_compact_write<<<nblocks, kCpT, 0, st>>>(bits, nwords, jmax, block_off, primes_out);
+    return cudaGetLastError();
+}
+
+__global__ void k_barrett(const uint32_t *primes, uint64_t n, uint64_t *m)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m[i] = 0xFFFFFFFFFFFFFFFFull / primes[i];
+}
+
+cudaError_t launch_barrett(const uint32_t *primes, uint64_t n, uint64_t *m, cudaStream_t st)
+{
+    k_barrett<<<1024, 256, 0, st>>>(primes, n, m);
+    return cudaGetLastError();
+}
+
+// sum of n uint32 counters into *acc (profiling: exact large-prime hit count)
+__global__ void k_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc)
+{
+    unsigned long long c = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(acc, c);
+}
+
+cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st)
+{
+    k_sum_u32<<<64, 256, 0, st>>>(v, n, acc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// popcount of a table
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc)
+{
+    unsigned long long c = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(words) & 15) == 0) {
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(words);
+        const uint64_t n4 = nwords / 4;
+        for (uint64_t i = i0; i < n4; i += stride) {
+            const uint4 v = __ldcs(w4 + i);
+            c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+        for (uint64_t i = 4 * n4 + i0; i < nwords; i += stride) c += __popc(words[i]);
+    } else {
+        for (uint64_t i = i0; i < nwords; i += stride) c += __popc(words[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(acc, c);
+}
+
+cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc, uint32_t grid,
+                            cudaStream_t st)
+{
+    k_popcount<<<grid, 512, 0, st>>>(words, nwords, acc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory atomic OR rate: every lane ORs into a random row of its own
+// bank (word = row*32 + lane), so a warp's 32 atomics never conflict
+// ---------------------------------------------------------------------------
+constexpr int kProbeWords = 32768;  // 128 KB, the size of a 2^20-bit tile
+constexpr int kProbeIters = 4096;
+
+__global__ void __launch_bounds__(1024) k_probe_smem(uint32_t *sink)
+{
+    extern __shared__ uint32_t pm[];
+    for (uint32_t i = threadIdx.x; i < kProbeWords; i += blockDim.x) pm[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t x = 0x9E3779B9u * (blockIdx.x * blockDim.x + threadIdx.x + 1);
+#pragma unroll 8
+    for (int it = 0; it < kProbeIters; ++it) {
+        x = x * 1664525u + 1013904223u;  // LCG (Numerical Recipes constants)
+        const uint32_t row = x >> 22;    // 0..1023
+        atomicOr(&pm[row * 32 + lane], 1u << (x & 31));
+    }
+    __syncthreads();
+    uint32_t v = 0;
+    for (uint32_t i = threadIdx.x; i < kProbeWords; i += blockDim.x) v ^= pm[i];
+    if (v == 0x12345678u) sink[0] = v;  // keeps the work observable
+}
+
+cudaError_t probe_smem_atomics(int nsm, double *atom_per_s)
+{
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 16);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)kProbeWords * 4;
+    cudaFuncSetAttribute(k_probe_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int grid = nsm;
+    k_probe_smem<<<grid, 1024, smem>>>(sink);  // warm-up
+    cudaEventRecord(a);
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) k_probe_smem<<<grid, 1024, smem>>>(sink);
+    cudaEventRecord(b);
+    e = cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    *atom_per_s = (double)grid * 1024.0 * kProbeIters * reps / (ms * 1e-3);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return e;
+}
+
+cudaError_t set_kernel_attributes()
+{
+    const int big = (int)tile_smem_bytes(20);
+    cudaError_t e = cudaFuncSetAttribute(k_tile<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
+    return e;
+}
+
+}  // namespace gbs

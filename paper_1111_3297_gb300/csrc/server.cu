@@ -1,0 +1,354 @@
+// Serving: a request loop with continuous batching.
+//
+// One scheduler thread owns all device work of the server.  Requests wait in a
+// FIFO; whenever a lane (a stream with its own scratch) is free, the scheduler
+// admits requests from the head of the FIFO while their tables fit in the
+// server's table arena, plans them as one batch (the batched path of
+// sieve_batch) and launches it on that lane.  Lanes run concurrently, so a
+// request that arrives while others are on the GPU starts as soon as a lane and
+// memory free up.  Completion is observed with cudaEventQuery (no blocking
+// waits), the composite counts come back in pinned memory, and the table stays
+// in the arena until the client releases it.
+#include "gbsieve.h"
+#include "host_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+using namespace gbs;
+
+namespace {
+
+constexpr uint64_t kGranule = 256;      // table arena granularity (bytes)
+constexpr uint32_t kMaxBatch = 1024;    // requests per launched batch
+constexpr uint64_t kMaxBatchBits = 1ull << 34;
+
+// first-fit allocator over [0, size) with coalescing free list
+struct Arena {
+    std::map<uint64_t, uint64_t> free_;  // offset -> size
+    uint64_t size = 0, used = 0;
+    void init(uint64_t n) {
+        size = n;
+        free_.clear();
+        free_[0] = n;
+        used = 0;
+    }
+    bool alloc(uint64_t n, uint64_t *off) {
+        n = (n + kGranule - 1) / kGranule * kGranule;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const uint64_t rest = it->second - n, o = it->first;
+                free_.erase(it);
+                if (rest) free_[o + n] = rest;
+                used += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n) {
+        n = (n + kGranule - 1) / kGranule * kGranule;
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Req {
+    uint64_t id, j0, nbits;
+    uint64_t off = 0, bytes = 0;  // table in the arena
+    uint64_t composites = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int status = SIEVE_OK;
+    bool done = false;
+};
+
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    Scratch scr;
+    unsigned long long *d_counts = nullptr;
+    unsigned long long *h_counts = nullptr;  // pinned
+    int *h_err = nullptr;                    // pinned
+    std::unique_ptr<Plan> plan;
+    std::vector<Req *> reqs;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct sieve_server {
+    sieve_ctx *c = nullptr;
+    uint32_t *d_arena = nullptr;
+    Arena arena;
+    std::vector<Lane> lanes;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> pending;
+    std::deque<Req *> done_q;
+    std::map<uint64_t, Req *> live;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    void loop();
+    bool launch(Lane &L, std::vector<Req *> &batch);
+    void complete(Lane &L);
+};
+
+bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
+{
+    std::vector<ReqSpec> rs(batch.size());
+    std::vector<uint64_t> vl(batch.size());
+    uint64_t vmax = 0;
+    for (size_t i = 0; i < batch.size(); ++i) {
+        rs[i] = ReqSpec{batch[i]->j0, batch[i]->nbits, batch[i]->off / 4, (uint32_t)i};
+        vl[i] = 2 * (batch[i]->j0 + batch[i]->nbits) - 1;
+        vmax = std::max(vmax, vl[i]);
+    }
+    std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
+    const sieve_tuning t = c->batch_tune.tile_log2 ? c->batch_tune : c->tune[tune_class(vmax)];
+    L.plan = build_plan(c, rs, t, L.scr.pool_entries);
+    Plan *P = L.plan.get();
+    sieve_status s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles);
+    if (!s) s = upload_plan(c, P, L.st);
+    if (!s) s = enqueue_plan(c, L.scr, P, d_arena, L.d_counts, (uint32_t)batch.size(), L.st);
+    if (!s && cudaMemcpyAsync(L.h_counts, L.d_counts, batch.size() * 8, cudaMemcpyDeviceToHost, L.st) != cudaSuccess)
+        s = SIEVE_ECUDA;
+    if (!s && cudaMemcpyAsync(L.h_err, L.scr.d_err, 4, cudaMemcpyDeviceToHost, L.st) != cudaSuccess) s = SIEVE_ECUDA;
+    if (!s && cudaMemsetAsync(L.scr.d_err, 0, 4, L.st) != cudaSuccess) s = SIEVE_ECUDA;
+    if (!s && cudaEventRecord(L.ev, L.st) != cudaSuccess) s = SIEVE_ECUDA;
+    L.reqs = batch;
+    L.busy = true;
+    if (s) {
+        // nothing (more) will run for these requests: finish them with the error
+        cudaStreamSynchronize(L.st);
+        for (Req *r : L.reqs) r->status = s;
+        *L.h_err = 0;
+        return false;
+    }
+    return true;
+}
+
+void sieve_server::complete(Lane &L)
+{
+    const double t = now();
+    const int err = *L.h_err;
+    std::lock_guard<std::mutex> g(mu);
+    for (size_t i = 0; i < L.reqs.size(); ++i) {
+        Req *r = L.reqs[i];
+        if (r->status == SIEVE_OK) {
+            r->composites = L.h_counts[i];
+            if (err) r->status = (err & kErrTimeout) ? SIEVE_ETIMEOUT : SIEVE_EOVERFLOW;
+        }
+        r->t_done = t;
+        r->done = true;
+        done_q.push_back(r);
+    }
+    L.reqs.clear();
+    L.plan.reset();
+    L.busy = false;
+    cv_done.notify_all();
+}
+
+void sieve_server::loop()
+{
+    cudaSetDevice(c->device);
+    for (;;) {
+        // 1. retire lanes whose work finished
+        for (Lane &L : lanes) {
+            if (!L.busy) continue;
+            const cudaError_t q = cudaEventQuery(L.ev);
+            if (q == cudaSuccess) {
+                complete(L);
+            } else if (q != cudaErrorNotReady) {
+                for (Req *r : L.reqs) r->status = SIEVE_ECUDA;
+                *L.h_err = 0;
+                complete(L);
+            }
+        }
+        // 2. admit from the head of the queue onto free lanes
+        bool launched = false;
+        for (Lane &L : lanes) {
+            if (L.busy) continue;
+            std::vector<Req *> batch;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                uint64_t bits = 0;
+                while (!pending.empty() && batch.size() < kMaxBatch && bits < kMaxBatchBits) {
+                    Req *r = pending.front();
+                    if (!arena.alloc(r->bytes, &r->off)) break;  // wait for memory
+                    pending.pop_front();
+                    r->t_admit = now();
+                    bits += r->nbits;
+                    batch.push_back(r);
+                }
+            }
+            if (batch.empty()) break;
+            if (!launch(L, batch)) complete(L);
+            launched = true;
+        }
+        // 3. sleep until new work or a short poll interval
+        std::unique_lock<std::mutex> g(mu);
+        bool any_busy = false;
+        for (Lane &L : lanes) any_busy |= L.busy;
+        if (stop && pending.empty() && !any_busy) break;
+        if (!launched) {
+            if (any_busy)
+                cv_work.wait_for(g, std::chrono::microseconds(50));
+            else
+                cv_work.wait_for(g, std::chrono::milliseconds(2), [&] { return stop || !pending.empty(); });
+        }
+    }
+}
+
+sieve_status sieve_server_create(sieve_ctx *c, size_t mem_cap, uint32_t max_inflight, sieve_server **out)
+{
+    if (!c || !out || max_inflight == 0 || max_inflight > 16 || mem_cap < ((size_t)256 << 20)) return SIEVE_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) return SIEVE_ECUDA;
+    std::unique_ptr<sieve_server> S(new sieve_server());
+    S->c = c;
+    S->t0 = std::chrono::steady_clock::now();
+    // a quarter of the cap for the lanes' bucket pools, the rest for tables
+    const uint64_t lane_pool = std::min<uint64_t>((uint64_t)4 << 30, mem_cap / 4 / max_inflight);
+    const uint64_t arena = mem_cap - lane_pool * max_inflight;
+    if (cudaMalloc(&S->d_arena, arena) != cudaSuccess) {
+        cudaGetLastError();
+        return SIEVE_ENOMEM;
+    }
+    S->arena.init(arena);
+    S->lanes.resize(max_inflight);
+    for (Lane &L : S->lanes) {
+        if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&L.d_counts, kMaxBatch * 8) != cudaSuccess ||
+            cudaMallocHost(&L.h_counts, kMaxBatch * 8) != cudaSuccess ||
+            cudaMallocHost(&L.h_err, 16) != cudaSuccess) {
+            cudaGetLastError();
+            sieve_server_destroy(S.release());
+            return SIEVE_ENOMEM;
+        }
+        *L.h_err = 0;
+        if (scratch_init(L.scr, lane_pool / 4, 1u << 20) != SIEVE_OK) {
+            sieve_server_destroy(S.release());
+            return SIEVE_ENOMEM;
+        }
+    }
+    sieve_server *raw = S.release();
+    raw->th = std::thread([raw] { raw->loop(); });
+    *out = raw;
+    return SIEVE_OK;
+}
+
+sieve_status sieve_server_submit(sieve_server *S, uint64_t j0, uint64_t nbits, uint64_t *id)
+{
+    if (!S || !id) return SIEVE_EINVAL;
+    uint64_t vlast;
+    sieve_status s = check_range(S->c, j0, nbits, &vlast);
+    if (s) return s;
+    if ((nbits / 8 + kGranule) > S->arena.size) return SIEVE_ENOMEM;
+    Req *r = new Req();
+    r->j0 = j0;
+    r->nbits = nbits;
+    r->bytes = nbits / 8;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->stop) {
+            delete r;
+            return SIEVE_EBUSY;
+        }
+        r->id = S->next_id++;
+        r->t_submit = S->now();
+        S->pending.push_back(r);
+        S->live[r->id] = r;
+    }
+    *id = r->id;
+    S->cv_work.notify_one();
+    return SIEVE_OK;
+}
+
+sieve_status sieve_server_poll(sieve_server *S, sieve_result *out, uint32_t max, uint32_t *n, uint32_t timeout_ms)
+{
+    if (!S || !n || (max && !out)) return SIEVE_EINVAL;
+    *n = 0;
+    std::unique_lock<std::mutex> g(S->mu);
+    if (S->done_q.empty() && timeout_ms)
+        S->cv_done.wait_for(g, std::chrono::milliseconds(timeout_ms), [&] { return !S->done_q.empty(); });
+    while (*n < max && !S->done_q.empty()) {
+        Req *r = S->done_q.front();
+        S->done_q.pop_front();
+        sieve_result &o = out[(*n)++];
+        o.id = r->id;
+        o.j0 = r->j0;
+        o.nbits = r->nbits;
+        o.composites = r->composites;
+        o.dev_bits = S->d_arena + r->off / 4;
+        o.t_submit = r->t_submit;
+        o.t_admit = r->t_admit;
+        o.t_done = r->t_done;
+        o.status = r->status;
+    }
+    return SIEVE_OK;
+}
+
+sieve_status sieve_server_release(sieve_server *S, uint64_t id)
+{
+    if (!S) return SIEVE_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->live.find(id);
+    if (it == S->live.end() || !it->second->done) return SIEVE_EINVAL;
+    S->arena.release(it->second->off, it->second->bytes);
+    delete it->second;
+    S->live.erase(it);
+    S->cv_work.notify_one();
+    return SIEVE_OK;
+}
+
+double sieve_server_now(sieve_server *S) { return S ? S->now() : 0.0; }
+
+void sieve_server_destroy(sieve_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    cudaSetDevice(S->c->device);
+    for (Lane &L : S->lanes) {
+        if (L.st) cudaStreamSynchronize(L.st);
+        L.plan.reset();
+        scratch_free(L.scr);
+        if (L.st) cudaStreamDestroy(L.st);
+        if (L.ev) cudaEventDestroy(L.ev);
+        if (L.d_counts) cudaFree(L.d_counts);
+        if (L.h_counts) cudaFreeHost(L.h_counts);
+        if (L.h_err) cudaFreeHost(L.h_err);
+    }
+    for (auto &kv : S->live) delete kv.second;
+    if (S->d_arena) cudaFree(S->d_arena);
+    delete S;
+}

@@ -1,0 +1,230 @@
+// Internal declarations of the GB300 sieve: descriptors, device helpers, launchers.
+//
+// Index space: absolute bit index J stands for the odd number 2J+1 (Sec. 1.2:
+// only odd numbers are represented).  A prime p divides 2J+1 exactly when
+// J = (p-1)/2 (mod p) (Lemma lem:q, Sec. 2.1), and its multiples are p apart in
+// index space (Sec. 1.3, after the Definition).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbs {
+
+// ---------------------------------------------------------------------------
+// Wheel W = {2,3,5} in index space (Sec. 3.2.1).  A multiple m = p*c (c odd) of a
+// prime p >= 7 is struck only when c is coprime to 15: multiples with 3 | c or
+// 5 | c are composites the pre-sieve already marked (3 and 5 are always in the
+// first pattern group).  Stepping c -> c+2 walks the residues mod 15; the
+// admissible ones, in walking order, form the cycle 1,7,11,13,2,4,8,14 with
+// gaps (in steps of c -> c+2, i.e. of p in index space) 3,2,1,2,1,2,3,1.
+// ---------------------------------------------------------------------------
+constexpr int kWheelCycle[8] = {1, 7, 11, 13, 2, 4, 8, 14};
+constexpr int kWheelGap[8] = {3, 2, 1, 2, 1, 2, 3, 1};
+
+constexpr bool wheel_admissible(int r) { return (r % 3) != 0 && (r % 5) != 0; }
+constexpr int wheel_pos(int r) {
+    for (int i = 0; i < 8; ++i)
+        if (kWheelCycle[i] == r) return i;
+    return -1;
+}
+// steps (c -> c+2) from residue r to the first admissible residue
+constexpr int wheel_skip(int r) {
+    int k = 0;
+    while (!wheel_admissible((r + 2 * k) % 15)) ++k;
+    return k;
+}
+constexpr uint32_t pack_gap() {
+    uint32_t x = 0;
+    for (int s = 0; s < 8; ++s) x |= (uint32_t)kWheelGap[s] << (2 * s);
+    return x;
+}
+constexpr uint32_t pack_skip() {
+    uint32_t x = 0;
+    for (int r = 0; r < 15; ++r) x |= (uint32_t)wheel_skip(r) << (2 * r);
+    return x;
+}
+constexpr uint64_t pack_state_after_skip() {
+    uint64_t x = 0;
+    for (int r = 0; r < 15; ++r)
+        x |= (uint64_t)wheel_pos((r + 2 * wheel_skip(r)) % 15) << (3 * r);
+    return x;
+}
+constexpr int inv_mod15(int a) {
+    for (int x = 1; x < 15; ++x)
+        if ((a * x) % 15 == 1) return x;
+    return 0;
+}
+constexpr uint64_t pack_inv15() {
+    uint64_t x = 0;
+    for (int r = 0; r < 15; ++r) x |= (uint64_t)inv_mod15(r) << (4 * r);
+    return x;
+}
+// cumulative gaps: cum(s, j) = sum_{t<j} gap[(s+t)&7], 4 bits per j
+constexpr uint32_t pack_cum(int s) {
+    uint32_t x = 0;
+    int c = 0;
+    for (int j = 0; j < 8; ++j) {
+        x |= (uint32_t)c << (4 * j);
+        c += kWheelGap[(s + j) & 7];
+    }
+    return x;
+}
+
+constexpr uint32_t kGapPacked = pack_gap();
+constexpr uint32_t kSkipPacked = pack_skip();
+constexpr uint64_t kStateAfterPacked = pack_state_after_skip();
+constexpr uint64_t kInv15Packed = pack_inv15();
+static_assert(kGapPacked == 0x799Bu, "wheel gap packing");
+static_assert(wheel_skip(0) == 1 && wheel_skip(3) == 2 && wheel_skip(10) == 2, "wheel skip");
+
+__device__ __forceinline__ uint32_t wheel_gap(uint32_t s) { return (kGapPacked >> (2 * s)) & 3u; }
+
+// ---------------------------------------------------------------------------
+// 64-bit remainder by a 32-bit odd prime p without a hardware divide: Barrett
+// reduction (P. Barrett, CRYPTO '86) with m = floor((2^64-1)/p) precomputed per
+// prime.  q' = floor(x*m / 2^64) satisfies floor(x/p) - 1 <= q' <= floor(x/p),
+// so r' = x - q'*p lies in [0, 2p) and one conditional subtraction finishes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t mod_barrett(uint64_t x, uint32_t p, uint64_t m)
+{
+    uint64_t q = __umul64hi(x, m);
+    uint64_t r = x - q * (uint64_t)p;
+    if (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+// First struck index at or after Js (relative offset h from Js) for prime p,
+// and the wheel state there.
+//   * Lemma lem:q: the first J >= Js with p | 2J+1 is Js + q with
+//     q = (p-1)/2 - (Js mod p)  (mod p).
+//   * Sec. 1.4: striking with p starts at p^2, whose index is (p^2-1)/2.
+//   * Sec. 3.2.1: then advance to the first multiple p*c with c coprime to 15.
+// js15 = Js mod 15.  Returns h as 64-bit (the p^2 start can lie far ahead).
+__device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32_t p, uint64_t m,
+                                              uint32_t &state)
+{
+    uint32_t r = mod_barrett(Js, p, m);
+    uint32_t half = p >> 1;
+    uint32_t q = (r <= half) ? (half - r) : (half + (p - r));
+    uint64_t jsq = ((uint64_t)p * p) >> 1;  // (p^2 - 1) / 2, p odd
+    uint64_t h;
+    uint32_t c15;
+    if (Js + q < jsq) {
+        h = jsq - Js;   // the number there is p*p, so c = p
+        c15 = p % 15u;
+    } else {
+        h = q;
+        // the number there is m = 2(Js+q)+1 = p*c, so c = m * p^{-1} (mod 15)
+        uint32_t m15 = (2u * js15 + 2u * (q % 15u) + 1u) % 15u;
+        uint32_t inv = (uint32_t)(kInv15Packed >> (4 * (p % 15u))) & 15u;
+        c15 = (m15 * inv) % 15u;
+    }
+    uint32_t sk = (kSkipPacked >> (2 * c15)) & 3u;
+    state = (uint32_t)(kStateAfterPacked >> (3 * c15)) & 7u;
+    return h + (uint64_t)sk * p;
+}
+
+// ---------------------------------------------------------------------------
+// Pre-sieve (Sec. 3.1): small primes are applied as periodic bit patterns.
+// Group g covers the primes whose product is P_g; bit rho (0 <= rho < P_g + 64)
+// of its pattern is 1 when some prime p of the group divides 2*rho+1 (rho = J
+// mod P_g).  A 32-bit window starting at rho is read with two loads and a
+// funnel shift.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPresieveGroups = 13;
+struct PresieveInfo {
+    uint32_t ngroups;                       // groups applied (1..13)
+    uint32_t modulus[kMaxPresieveGroups];   // P_g
+    uint32_t word_off[kMaxPresieveGroups];  // offset of the group's pattern in the table
+    uint32_t max_prime;                     // largest prime covered by the applied groups
+};
+
+// ---------------------------------------------------------------------------
+// Work descriptors.
+// ---------------------------------------------------------------------------
+struct TileDesc {
+    uint64_t J;         // absolute index of the tile's first bit (multiple of 32)
+    uint64_t out_word;  // word offset of the tile in the output buffer
+    uint64_t bkt_off;   // entry offset of the tile's large-prime bucket in the pool
+    uint32_t len;       // bits in the tile (multiple of 32, <= 2^tile_log2)
+    uint32_t req;       // request index (for per-request counts)
+    uint32_t bkt_cap;   // bucket capacity in entries (0: no large primes)
+    uint32_t med_hi;    // medium primes used: base indices [med_lo, med_hi)
+};
+static_assert(sizeof(TileDesc) == 40, "TileDesc layout");
+
+struct SUDesc {         // scatter unit: consecutive tiles of one request inside a group
+    uint64_t J;         // absolute index of the first bit (start of a tile)
+    uint32_t span;      // bits covered (<= 2^30)
+    uint32_t tile_rel;  // index of its first tile relative to the group's first tile
+    uint32_t plimit;    // largest prime that may strike (isqrt of the request's last number)
+    uint32_t pad;
+};
+static_assert(sizeof(SUDesc) == 24, "SUDesc layout");
+
+struct GroupDesc {      // scatter units sharing one flush domain (<= kScatterMaxTiles tiles)
+    uint32_t su0, nsu;
+    uint32_t tile0, ntiles;  // tiles [tile0, tile0+ntiles) of the launch's tile list
+    uint32_t p_lo, p_hi;     // large primes: base indices [p_lo, p_hi)
+};
+
+constexpr uint32_t kStateInf = 0xFFFFFFFFu;
+
+// device error bits
+constexpr int kErrOverflow = 1;
+constexpr int kErrTimeout = 2;
+
+struct TileArgs {
+    const TileDesc *tiles;
+    uint32_t ntiles;
+    uint32_t *work;                 // persistent-grid work counter (zeroed before launch)
+    const uint32_t *primes;
+    const uint64_t *barrett;
+    uint32_t med_lo, coop_hi;       // medium primes start at med_lo; warp-cooperative below coop_hi
+    const uint32_t *pat;
+    PresieveInfo ps;
+    const uint32_t *bkt;            // bucket pool
+    const uint32_t *bkt_cnt;        // entries per tile (indexed like tiles)
+    const unsigned long long *ovf;  // overflow list: (tile << 32) | offset
+    const uint32_t *ovf_cnt;
+    uint32_t ovf_cap;
+    uint32_t *out;
+    unsigned long long *req_counts; // may be null
+    uint32_t tile_log2;
+};
+
+struct ScatterArgs {
+    const uint32_t *primes;
+    const uint64_t *barrett;
+    const SUDesc *sus;
+    const GroupDesc *groups;
+    const TileDesc *tiles;          // bucket offset and capacity of every tile
+    uint32_t *bkt;
+    uint32_t *bkt_cnt;
+    unsigned long long *ovf;
+    uint32_t *ovf_cnt;
+    uint32_t ovf_cap;
+    int *err;
+    uint32_t tile_log2;
+};
+
+// launchers (kernels.cu)
+int tile_threads(uint32_t tile_log2);
+int tile_blocks_per_sm(uint32_t tile_log2);
+size_t tile_smem_bytes(uint32_t tile_log2);
+cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
+constexpr uint32_t kScatterChunk = 16384;    // primes per scatter CTA
+constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, uint32_t ngroups, cudaStream_t st);
+cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
+cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
+                           uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out,
+                           cudaStream_t st);
+cudaError_t launch_barrett(const uint32_t *primes, uint64_t n, uint64_t *m, cudaStream_t st);
+cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc,
+                            uint32_t grid, cudaStream_t st);
+cudaError_t probe_smem_atomics(int nsm, double *atom_per_s);
+cudaError_t set_kernel_attributes();
+cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st);
+
+}  // namespace gbs

@@ -1,0 +1,291 @@
+"""Python binding of libgbsieve.so (include/gbsieve.h): argument marshalling only.
+
+Every function has the C name and forwards to the C ABI; all sieving runs in
+the library's CUDA kernels.  Device buffers are torch CUDA tensors (int32 words,
+bit j = bit j%32 of word j//32), streams are torch.cuda.Stream objects (default:
+the current stream).  There is no CPU fallback: if the library is missing or
+fails to load, every call raises.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_PKG, "libgbsieve.so")
+_lib = None
+
+_u32, _u64, _i32, _vp, _dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+
+STATUS = {0: "SIEVE_OK", 1: "SIEVE_EINVAL", 2: "SIEVE_ERANGE", 3: "SIEVE_ENOMEM", 4: "SIEVE_ECUDA",
+          5: "SIEVE_ETIMEOUT", 6: "SIEVE_EBUSY", 7: "SIEVE_EOVERFLOW"}
+
+K_TILE, K_SCATTER, K_COUNT, K_RESET, K_COPY = 0, 1, 2, 3, 4
+
+
+class SieveError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), lib().sieve_strerror(status).decode()))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_log2", _u32), ("presieve_groups", _u32), ("coop_max", _u32),
+                ("medium_max", _u32), ("window_tiles", _u32), ("epoch_tiles", _u32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Req(ctypes.Structure):
+    _fields_ = [("j0", _u64), ("nbits", _u64), ("out_word_off", _u64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", _u64 * 8), ("ms", _dbl * 8), ("tiles", _u64), ("bits", _u64),
+                ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", _u64), ("j0", _u64), ("nbits", _u64), ("composites", _u64),
+                ("dev_bits", _vp), ("t_submit", _dbl), ("t_admit", _dbl), ("t_done", _dbl),
+                ("status", _i32)]
+
+
+def lib():
+    """Load libgbsieve.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError("libgbsieve.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(_LIBPATH)
+        sig = {
+            "sieve_strerror": (ctypes.c_char_p, [_i32]),
+            "sieve_init": (_i32, [ctypes.POINTER(_vp), _i32, _u64, ctypes.c_size_t]),
+            "sieve_destroy": (None, [_vp]),
+            "sieve_segments": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp]),
+            "sieve_f_from_midpoint": (_i32, [_u32, _u64, _u64, _u32, ctypes.POINTER(_u64)]),
+            "sieve_segments_midpoint": (_i32, [_vp, _u32, _u64, _u32, _u64, _vp, _vp]),
+            "sieve_segments_host": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp]),
+            "sieve_count": (_i32, [_vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
+            "sieve_sync": (_i32, [_vp, _vp]),
+            "sieve_batch": (_i32, [_vp, ctypes.POINTER(Req), _u32, _vp, _vp, _vp]),
+            "sieve_get_tuning": (_i32, [_vp, _u32, ctypes.POINTER(Tuning)]),
+            "sieve_set_tuning": (_i32, [_vp, _u32, ctypes.POINTER(Tuning)]),
+            "sieve_autotune": (_i32, [_vp, _u32, _u64, _u64, ctypes.POINTER(Tuning), _vp]),
+            "sieve_autotune_batch": (_i32, [_vp, ctypes.POINTER(Req), _u32, _vp, _vp,
+                                            ctypes.POINTER(Tuning), _vp]),
+            "sieve_base_info": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+            "sieve_profile_enable": (_i32, [_vp, _i32]),
+            "sieve_profile_read": (_i32, [_vp, ctypes.POINTER(Profile), _vp]),
+            "sieve_probe_smem_atomics": (_i32, [_i32, ctypes.POINTER(_dbl)]),
+            "sieve_server_create": (_i32, [_vp, ctypes.c_size_t, _u32, ctypes.POINTER(_vp)]),
+            "sieve_server_submit": (_i32, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
+            "sieve_server_poll": (_i32, [_vp, ctypes.POINTER(Result), _u32, ctypes.POINTER(_u32), _u32]),
+            "sieve_server_release": (_i32, [_vp, _u64]),
+            "sieve_server_now": (_dbl, [_vp]),
+            "sieve_server_destroy": (None, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st, where):
+    if st != 0:
+        raise SieveError(st, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, what):
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return _vp(t.data_ptr())
+
+
+class Ctx:
+    """A context (resident base primes and scratch) on one device."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().sieve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sieve_init(device=0, max_v=(1 << 62), mem_budget=0):
+    h = _vp()
+    _check(lib().sieve_init(ctypes.byref(h), device, max_v, mem_budget), "sieve_init")
+    return Ctx(h, device)
+
+
+def sieve_destroy(ctx):
+    ctx.close()
+
+
+def sieve_segments(ctx, l, f, n, dev_bits, stream=None):
+    _check(lib().sieve_segments(ctx.handle, l, f, n, _dev_ptr(dev_bits, "dev_bits"), _stream(stream)),
+           "sieve_segments")
+
+
+def sieve_f_from_midpoint(l, n, mant, exp10):
+    out = _u64()
+    _check(lib().sieve_f_from_midpoint(l, n, mant, exp10, ctypes.byref(out)), "sieve_f_from_midpoint")
+    return out.value
+
+
+def sieve_segments_midpoint(ctx, l, mant, exp10, n, dev_bits, stream=None):
+    _check(lib().sieve_segments_midpoint(ctx.handle, l, mant, exp10, n, _dev_ptr(dev_bits, "dev_bits"),
+                                         _stream(stream)), "sieve_segments_midpoint")
+
+
+def sieve_segments_host(ctx, l, f, n, host_bits, stream=None):
+    """host_bits: a CPU torch tensor or numpy array of n*2^(l-5) 32-bit words."""
+    if hasattr(host_bits, "data_ptr"):
+        if host_bits.is_cuda or not host_bits.is_contiguous():
+            raise TypeError("host_bits must be a contiguous CPU tensor")
+        ptr = host_bits.data_ptr()
+    else:
+        ptr = host_bits.ctypes.data
+    _check(lib().sieve_segments_host(ctx.handle, l, f, n, _vp(ptr), _stream(stream)), "sieve_segments_host")
+
+
+def sieve_count(ctx, dev_bits, nbits, stream=None):
+    out = _u64()
+    _check(lib().sieve_count(ctx.handle, _dev_ptr(dev_bits, "dev_bits"), nbits, ctypes.byref(out),
+                             _stream(stream)), "sieve_count")
+    return out.value
+
+
+def sieve_sync(ctx, stream=None):
+    _check(lib().sieve_sync(ctx.handle, _stream(stream)), "sieve_sync")
+
+
+def _reqs(reqs):
+    arr = (Req * len(reqs))()
+    for i, r in enumerate(reqs):
+        arr[i].j0, arr[i].nbits, arr[i].out_word_off = int(r[0]), int(r[1]), int(r[2])
+    return arr
+
+
+def sieve_batch(ctx, reqs, dev_arena, dev_counts, stream=None):
+    """reqs: sequence of (j0, nbits, out_word_off); dev_counts: CUDA int64 tensor (len(reqs),)."""
+    arr = _reqs(reqs)
+    _check(lib().sieve_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena"),
+                             _dev_ptr(dev_counts, "dev_counts"), _stream(stream)), "sieve_batch")
+
+
+def sieve_get_tuning(ctx, cls):
+    t = Tuning()
+    _check(lib().sieve_get_tuning(ctx.handle, cls, ctypes.byref(t)), "sieve_get_tuning")
+    return t.as_dict()
+
+
+def sieve_set_tuning(ctx, cls, **kw):
+    t = Tuning()
+    _check(lib().sieve_get_tuning(ctx.handle, cls, ctypes.byref(t)), "sieve_get_tuning")
+    for k, v in kw.items():
+        setattr(t, k, v)
+    _check(lib().sieve_set_tuning(ctx.handle, cls, ctypes.byref(t)), "sieve_set_tuning")
+
+
+def sieve_autotune(ctx, l, f, n, stream=None):
+    t = Tuning()
+    _check(lib().sieve_autotune(ctx.handle, l, f, n, ctypes.byref(t), _stream(stream)), "sieve_autotune")
+    return t.as_dict()
+
+
+def sieve_autotune_batch(ctx, reqs, dev_arena, dev_counts, stream=None):
+    t = Tuning()
+    arr = _reqs(reqs)
+    _check(lib().sieve_autotune_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena"),
+                                      _dev_ptr(dev_counts, "dev_counts"), ctypes.byref(t), _stream(stream)),
+           "sieve_autotune_batch")
+    return t.as_dict()
+
+
+def sieve_base_info(ctx):
+    p, c, lim = _vp(), _u64(), _u64()
+    _check(lib().sieve_base_info(ctx.handle, ctypes.byref(p), ctypes.byref(c), ctypes.byref(lim)),
+           "sieve_base_info")
+    return p.value, c.value, lim.value
+
+
+def sieve_profile_enable(ctx, enable=True):
+    _check(lib().sieve_profile_enable(ctx.handle, 1 if enable else 0), "sieve_profile_enable")
+
+
+def sieve_profile_read(ctx, stream=None):
+    p = Profile()
+    _check(lib().sieve_profile_read(ctx.handle, ctypes.byref(p), _stream(stream)), "sieve_profile_read")
+    return {"launches": list(p.launches), "ms": list(p.ms), "tiles": p.tiles, "bits": p.bits,
+            "large_hits": p.large_hits, "medium_marks": p.medium_marks, "prime_reads": p.prime_reads}
+
+
+def sieve_probe_smem_atomics(device=0):
+    r = _dbl()
+    _check(lib().sieve_probe_smem_atomics(device, ctypes.byref(r)), "sieve_probe_smem_atomics")
+    return r.value
+
+
+class Server:
+    """Continuous-batching request loop (sieve_server_*)."""
+
+    def __init__(self, ctx, mem_cap, max_inflight=4):
+        self.ctx = ctx  # keeps the context alive
+        h = _vp()
+        _check(lib().sieve_server_create(ctx.handle, mem_cap, max_inflight, ctypes.byref(h)), "sieve_server_create")
+        self.handle = h
+
+    def submit(self, j0, nbits):
+        out = _u64()
+        _check(lib().sieve_server_submit(self.handle, j0, nbits, ctypes.byref(out)), "sieve_server_submit")
+        return out.value
+
+    def poll(self, max_results=256, timeout_ms=0):
+        buf = (Result * max_results)()
+        n = _u32()
+        _check(lib().sieve_server_poll(self.handle, buf, max_results, ctypes.byref(n), timeout_ms),
+               "sieve_server_poll")
+        return [{"id": r.id, "j0": r.j0, "nbits": r.nbits, "composites": r.composites,
+                 "dev_bits": r.dev_bits, "t_submit": r.t_submit, "t_admit": r.t_admit,
+                 "t_done": r.t_done, "status": r.status} for r in buf[:n.value]]
+
+    def release(self, rid):
+        _check(lib().sieve_server_release(self.handle, rid), "sieve_server_release")
+
+    def now(self):
+        return lib().sieve_server_now(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().sieve_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sieve_server_create(ctx, mem_cap, max_inflight=4):
+    return Server(ctx, mem_cap, max_inflight)

@@ -1,0 +1,66 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function that
+include/*.h declares (no device calls: runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("sieve_") and not name.endswith("_t"):
+                names.add(name)
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import shutil
+    from paper_1111_3297_gb300 import build
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc") \
+            and not os.path.exists(build.LIB):
+        pytest.skip("no nvcc to build the library")
+    return ctypes.CDLL(build.build_library())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["sieve_init", "sieve_segments", "sieve_count", "sieve_f_from_midpoint",
+                 "sieve_segments_midpoint", "sieve_batch", "sieve_destroy", "sieve_strerror",
+                 "sieve_server_create", "sieve_autotune"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_function(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points_work_without_a_gpu(lib):
+    lib.sieve_strerror.restype = ctypes.c_char_p
+    assert lib.sieve_strerror(0) == b"ok"
+    assert b"overflow" in lib.sieve_strerror(7)
+    f = ctypes.c_uint64()
+    lib.sieve_f_from_midpoint.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint64)]
+    assert lib.sieve_f_from_midpoint(20, 32768, 1 << 60, 0, ctypes.byref(f)) == 0
+    assert f.value == 2**39 - 16384
+    assert lib.sieve_f_from_midpoint(4, 1, 1, 0, ctypes.byref(f)) == 1
+    assert lib.sieve_f_from_midpoint(20, 1, 5, 19, ctypes.byref(f)) == 2  # 5e19 > 2^64
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    from paper_1111_3297_gb300 import sieve as S
+    monkeypatch.setattr(S, "_lib", None)
+    monkeypatch.setattr(S, "_LIBPATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        S.lib()

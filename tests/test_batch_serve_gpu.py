@@ -1,0 +1,155 @@
+"""Batched and served forms on the GPU, bit-exact against stored oracle values and
+against the plain per-interval calls."""
+import hashlib
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_1111_3297_gb300 import sieve as S
+from paper_1111_3297_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_3297_gb300 import build
+    build.build_library()
+    c = S.sieve_init(0, max_v=1 << 62)
+    yield c
+    c.close()
+
+
+class _DevArray:
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, True), "version": 3}
+
+
+def sha(t):
+    return hashlib.sha256(t.cpu().numpy().tobytes()).hexdigest()
+
+
+def golden_batch():
+    rows = []
+    with open(os.path.join(GOLDEN, "batch_4096_seed0.txt")) as fh:
+        for ln in fh:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            i, j0, nb, cnt, h = ln.split()
+            rows.append((int(j0), int(nb), int(cnt), h))
+    return rows
+
+
+def layout(reqs, align_words=1):
+    out, off = [], 0
+    for j0, nb in reqs:
+        out.append((j0, nb, off))
+        off += (nb // 32 + align_words - 1) // align_words * align_words
+    return out, off
+
+
+def test_batch_4096_every_request_bit_exact(ctx):
+    rows = golden_batch()
+    reqs = [(j0, nb) for j0, nb, _, _ in rows]
+    assert reqs == workloads.batch_requests(4096, seed=0)
+    lay, total = layout(reqs)
+    arena = torch.empty(total, dtype=torch.int32, device="cuda")
+    counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
+    for _ in range(2):  # direct launches, then the captured graph
+        arena.fill_(-1)
+        counts.fill_(-1)
+        S.sieve_batch(ctx, lay, arena, counts)
+        S.sieve_sync(ctx)
+        got = counts.cpu().numpy()
+        want = np.array([c for _, _, c, _ in rows])
+        bad = np.nonzero(got != want)[0]
+        assert len(bad) == 0, "requests with wrong counts: %s" % bad[:10]
+    for (j0, nb, off), (_, _, _, h) in zip(lay, rows):
+        assert sha(arena[off:off + nb // 32]) == h, (j0, nb)
+
+
+def test_batch_equals_plain_calls_on_unaligned_offsets(ctx):
+    reqs = workloads.batch_requests(96, seed=5)
+    lay, total = layout(reqs)
+    lay = [(j0, nb, off + 1) for j0, nb, off in lay]  # odd word offsets: no 16-byte alignment
+    arena = torch.zeros(total + 1, dtype=torch.int32, device="cuda")
+    counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
+    S.sieve_batch(ctx, lay, arena, counts)
+    S.sieve_sync(ctx)
+    for (j0, nb, off), c in zip(lay, counts.cpu().tolist()):
+        plain = torch.empty(nb // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments(ctx, 5, j0 // 32, nb // 32, plain)
+        S.sieve_sync(ctx)
+        assert torch.equal(plain, arena[off:off + nb // 32]), (j0, nb)
+        assert S.sieve_count(ctx, plain, nb) == c
+
+
+def test_batch_autotune_keeps_bits(ctx):
+    reqs = workloads.batch_requests(256, seed=3)
+    lay, total = layout(reqs, 4)
+    arena = torch.empty(total, dtype=torch.int32, device="cuda")
+    counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
+    S.sieve_batch(ctx, lay, arena, counts)
+    S.sieve_sync(ctx)
+    ref_counts, ref_sha = counts.clone(), sha(arena)
+    t = S.sieve_autotune_batch(ctx, lay, arena, counts)
+    assert 16 <= t["tile_log2"] <= 20
+    arena.fill_(0)
+    S.sieve_batch(ctx, lay, arena, counts)
+    S.sieve_sync(ctx)
+    assert torch.equal(counts, ref_counts) and sha(arena) == ref_sha
+
+
+def test_serving_results_equal_alone_and_in_the_mix(ctx):
+    rng = workloads.SplitMix64(77)
+    reqs = [r for r in workloads.batch_requests(400, seed=9) if r[1] <= (1 << 22)][:160]
+    srv = S.Server(ctx, mem_cap=4 << 30, max_inflight=4)
+    try:
+        def table(res):
+            return torch.as_tensor(_DevArray(res["dev_bits"], res["nbits"] // 32), device="cuda").clone()
+
+        alone = {}
+        for j0, nb in reqs[:24]:  # one at a time: nothing else on the device
+            rid = srv.submit(j0, nb)
+            got = []
+            while not got:
+                got = srv.poll(8, timeout_ms=2000)
+            assert len(got) == 1 and got[0]["id"] == rid and got[0]["status"] == 0
+            alone[(j0, nb)] = (got[0]["composites"], sha(table(got[0])))
+            srv.release(rid)
+        # the same requests again, inside a stream of others arriving meanwhile
+        order = list(range(len(reqs)))
+        for i in range(len(order) - 1, 0, -1):
+            k = rng.below(i + 1)
+            order[i], order[k] = order[k], order[i]
+        ids = {}
+        for i in order:
+            ids[srv.submit(*reqs[i])] = reqs[i]
+            if rng.below(4) == 0:
+                time.sleep(0.0005)
+        results = {}
+        deadline = time.time() + 120
+        while len(results) < len(ids) and time.time() < deadline:
+            for r in srv.poll(256, timeout_ms=100):
+                assert r["status"] == 0
+                results[r["id"]] = (r["composites"], sha(table(r)))
+                srv.release(r["id"])
+        assert len(results) == len(ids)
+        for rid, key in ids.items():
+            if key in alone:
+                assert results[rid] == alone[key], key
+        # and every served result equals the plain call
+        for rid, (j0, nb) in list(ids.items())[:40]:
+            plain = torch.empty(nb // 32, dtype=torch.int32, device="cuda")
+            S.sieve_segments(ctx, 5, j0 // 32, nb // 32, plain)
+            S.sieve_sync(ctx)
+            assert results[rid][1] == sha(plain)
+    finally:
+        srv.close()
