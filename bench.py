@@ -39,7 +39,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-plain", action="store_true", help="also time the batch as per-request calls")
+    ap.add_argument("--segments", type=int, default=0, help="override n (small profiling cases)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -189,6 +192,101 @@ def cpu_baseline(wl, f):
                       % (sample, n, l, dt, cores)}
 
 
+def measure_batch(S, ctx, args, rank, world):
+    """4096 seeded requests of uneven length (2^16..2^28 numbers) and magnitude
+    (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
+    plain form (one sieve_segments call per request), same outputs, same GPU."""
+    import torch
+    from paper_1111_3297_gb300 import workloads
+    reqs = workloads.batch_requests(4096, seed=rank)
+    lay, off = [], 0
+    for j0, nb in reqs:
+        lay.append((j0, nb, off))
+        off += (nb // 32 + 3) // 4 * 4
+    bits = sum(nb for _, nb in reqs)
+    arena = torch.empty(off, dtype=torch.int32, device="cuda")
+    counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    tuned = S.sieve_autotune_batch(ctx, lay, arena, counts) if not args.no_autotune else None
+    t_tune = time.perf_counter() - t0
+    for _ in range(3):
+        S.sieve_batch(ctx, lay, arena, counts)
+    S.sieve_sync(ctx)
+    ksteps = max(2, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(ksteps):
+        S.sieve_batch(ctx, lay, arena, counts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3 / ksteps
+    ref = counts.cpu().clone()
+    # plain: one call per request into the same arena slots
+    for j0, nb, o in lay:
+        S.sieve_segments(ctx, 5, j0 // 32, nb // 32, arena[o:o + nb // 32])
+    S.sieve_sync(ctx)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j0, nb, o in lay:
+        S.sieve_segments(ctx, 5, j0 // 32, nb // 32, arena[o:o + nb // 32])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    same = all(S.sieve_count(ctx, arena[o:o + nb // 32], nb) == int(c)
+               for (j0, nb, o), c in zip(lay[:256], ref.tolist()[:256]))
+    del arena, counts
+    torch.cuda.empty_cache()
+    return {"requests": len(reqs), "odd_numbers": bits, "batched": bits / t_batch, "plain": bits / t_plain,
+            "unit": "odd numbers/s", "speedup": t_plain / t_batch, "batched_ms": t_batch * 1e3,
+            "plain_ms": t_plain * 1e3, "same_counts_first256": same, "tuning": tuned,
+            "autotune_s": t_tune}
+
+
+def measure_serving(S, ctx, args, rank):
+    """Seeded Poisson arrivals (2000 requests/s) of requests drawn as in the batch,
+    admission capped by 64 GB of device memory; p50/p99 latency (submit -> done)
+    and sustained odd numbers/s."""
+    from paper_1111_3297_gb300 import workloads
+    rate = 2000.0
+    count = int(rate * args.serve_seconds)
+    reqs = workloads.batch_requests(count, seed=100 + rank)
+    arrivals = workloads.poisson_arrivals(count, rate, seed=rank)
+    srv = S.Server(ctx, mem_cap=64 << 30, max_inflight=4)
+    lat, done_bits, first, last = [], 0, None, 0.0
+    try:
+        i = 0
+        t_start = srv.now()
+        pending = 0
+        while i < count or pending:
+            now = srv.now() - t_start
+            while i < count and arrivals[i] <= now:
+                srv.submit(*reqs[i])
+                pending += 1
+                i += 1
+            for r in srv.poll(1024, timeout_ms=0 if i < count else 50):
+                if r["status"] != 0:
+                    raise RuntimeError("served request failed with status %d" % r["status"])
+                lat.append(r["t_done"] - r["t_submit"])
+                done_bits += r["nbits"]
+                first = r["t_submit"] if first is None else min(first, r["t_submit"])
+                last = max(last, r["t_done"])
+                srv.release(r["id"])
+                pending -= 1
+            if i < count:
+                nxt = arrivals[i] - (srv.now() - t_start)
+                if nxt > 0.0002:
+                    time.sleep(min(nxt, 0.001))
+    finally:
+        srv.close()
+    lat.sort()
+    q = lambda x: lat[min(len(lat) - 1, int(x * len(lat)))]  # noqa: E731
+    return {"requests": count, "rate_per_s": rate, "p50_ms": q(0.50) * 1e3, "p99_ms": q(0.99) * 1e3,
+            "max_ms": lat[-1] * 1e3, "sustained": done_bits / (last - first), "unit": "odd numbers/s",
+            "offered": sum(nb for _, nb in reqs) / arrivals[-1], "mem_cap_gb": 64, "lanes": 4}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -211,11 +309,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
 
+    from paper_1111_3297_gb300 import shard
     l, n = wl["l"], wl["n"]
+    if args.segments:
+        n = args.segments
     f0 = wl.get("f")
     if f0 is None:
         f0 = S.sieve_f_from_midpoint(l, n, wl["mant"], wl["exp10"])
-    f = f0 + rank * n  # weak scaling: each rank its own n segments
+    f, _ = shard.shard(l, f0, n, rank, world, "weak")  # each rank its own n segments
     N = n << l
     J0 = f << l
     vmax = 2 * ((f0 + world * n) << l)
@@ -260,7 +361,7 @@ def main():
         ms_max = float(t.item())
     value = world * N * args.steps / (ms_max * 1e-3)
 
-    composites = S.sieve_count(ctx, out, N)
+    composites = shard.total_count(S.sieve_count(ctx, out, N))
 
     # ---- end to end: the table delivered to pinned host memory ----
     e2e = None
@@ -337,7 +438,15 @@ def main():
 
     base_line = None
     if rank == 0 and not args.no_cpu_baseline:
-        base_line = cpu_baseline(wl, f0)
+        base_line = cpu_baseline(dict(wl, n=n), f0)
+    del out
+    torch.cuda.empty_cache()
+    batch = None
+    if not args.no_batch:
+        batch = measure_batch(S, ctx, args, rank, world)
+    serving = None
+    if not args.no_serve:
+        serving = measure_serving(S, ctx, args, rank)
 
     if rank == 0:
         print(json.dumps({
@@ -351,6 +460,7 @@ def main():
             "gpu_launches": int(sum(prof["launches"])),
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "cpu_baseline": base_line, "e2e": e2e, "clocks": clk,
+            "batch": batch, "serving": serving,
             "composites": composites, "smem_atomic_peak_per_s": r_atom,
         }), flush=True)
     ctx.close()

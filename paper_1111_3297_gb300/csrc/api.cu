@@ -724,7 +724,7 @@ Plan *cached_plan(sieve_ctx *c, const std::string &key, const std::vector<ReqSpe
 {
     auto it = c->plans.find(key);
     if (it != c->plans.end()) return it->second.get();
-    if (c->plans.size() >= 64) {
+    if (c->plans.size() >= 8192) {
         cudaDeviceSynchronize();
         c->plans.clear();
     }

@@ -60,7 +60,7 @@ class _DevArray:
     """Wraps a device pointer for torch.as_tensor (CUDA array interface, zero copy)."""
 
     def __init__(self, ptr, n):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False),
                                          "version": 3}
 
 
