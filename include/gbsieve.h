@@ -99,6 +99,26 @@ sieve_status sieve_segments_host(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_
 sieve_status sieve_count(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t nbits,
                          uint64_t *host_count, sieve_stream stream);
 
+/*
+ * Composite count without any allocation (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory: code whose device
+ * memory is owned by another framework's pool, and latency-critical code that
+ * must not risk the implicit device synchronisation of cudaMalloc/cudaFree).
+ * Needs no context.  Counts the 1 bits of the first nbits bits of dev_bits
+ * (nbits % 32 == 0, at most SIEVE_NOALLOC_MAX_BITS, else SIEVE_ERANGE) on the
+ * current device and writes the count to the caller-owned device word
+ * *dev_count, asynchronously on `stream`.  Its only scratch is a fixed 512 KB
+ * array of partial counts inside the library, which every GPU that loads the
+ * library holds until the process exits.  The first call on a device resolves
+ * that array's device address (a one-time set-up with the device current); make
+ * the first call on each device before any stream capture.  All calls share the
+ * array and each overwrites the entries it uses, so calls that overlap on the
+ * GPU (e.g. on two streams at once) race and must be ordered by the caller.
+ */
+#define SIEVE_NOALLOC_MAX_BITS (1ull << 37)
+sieve_status sieve_count_noalloc(const uint32_t *dev_bits, uint64_t nbits, uint64_t *dev_count,
+                                 sieve_stream stream);
+
 /* Wait for `stream` and report any device-side error recorded since the last wait. */
 sieve_status sieve_sync(sieve_ctx *ctx, sieve_stream stream);
 
