@@ -320,7 +320,9 @@ def main():
     N = n << l
     J0 = f << l
     vmax = 2 * ((f0 + world * n) << l)
-    ctx = S.sieve_init(local, max_v=vmax)
+    # the batch and serving legs draw requests up to ~1e18
+    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 30)) if not (args.no_batch and args.no_serve)
+                       else vmax)
     stream = torch.cuda.current_stream()
     out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
 

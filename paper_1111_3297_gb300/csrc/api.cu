@@ -212,6 +212,57 @@ sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoc
 // buckets: their tiles are grouped into scatter groups (<= window_tiles tiles,
 // runs of one request form a scatter unit) and groups into epochs whose bucket
 // capacity fits the pool.  Per epoch: scatter launch, then tile launch.
+// Scatter chunks: each CTA takes a run of large primes of one group.  Runs are
+// cut so that every chunk of an epoch carries about the same estimated work: a
+// first-hit computation per (prime, scatter unit) plus the prime's hits, which
+// number span*(8/15)/p (the wheel keeps 8 of 15 multiples).  Small large primes
+// have many hits each, so their chunks hold few primes.
+static void make_chunks(sieve_ctx *c, Plan *P)
+{
+    const double kFirstHitCost = 2.0;  // one first hit ~ two emitted hits
+    for (Plan::Epoch &e : P->epochs) {
+        e.c0 = (uint32_t)P->chunks.size();
+        e.nc = 0;
+        if (!e.ng) continue;
+        // a chunk walks every group of the epoch: its cost is summed over groups
+        std::vector<double> span(e.ng, 0.0);
+        uint32_t plo = ~0u, phi = 0;
+        for (uint32_t g = 0; g < e.ng; ++g) {
+            const GroupDesc &G = P->groups[e.g0 + g];
+            for (uint32_t k = 0; k < G.nsu; ++k) span[g] += P->sus[G.su0 + k].span;
+            plo = std::min(plo, G.p_lo);
+            phi = std::max(phi, G.p_hi);
+        }
+        auto cost = [&](uint32_t i, uint32_t j) {
+            double x = 0;
+            for (uint32_t g = 0; g < e.ng; ++g) {
+                const GroupDesc &G = P->groups[e.g0 + g];
+                const uint32_t a = std::max(i, G.p_lo), b = std::min(j, G.p_hi);
+                if (a >= b) continue;
+                x += kFirstHitCost * G.nsu * (double)(b - a) + span[g] * (8.0 / 15.0) * inv_sum(c, a, b);
+            }
+            return x;
+        };
+        const double target = std::max(cost(plo, phi) / (8.0 * c->nsm), 65536.0);
+        uint32_t i = plo;
+        while (i < phi) {
+            // smallest j (step 32, at most 65536 primes) with cost(i, j) >= target
+            uint32_t lo = 1, hi = std::max<uint32_t>(1, std::min<uint32_t>(2048, (phi - i + 31) / 32));
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) / 2;
+                if (cost(i, std::min(phi, i + 32 * mid)) >= target)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const uint32_t j = std::min(phi, i + 32 * lo);
+            P->chunks.push_back(ChunkDesc{i, j});
+            e.nc++;
+            i = j;
+        }
+    }
+}
+
 std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tuning t, uint64_t pool_cap_in)
 {
     std::unique_ptr<Plan> P(new Plan());
@@ -226,6 +277,12 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     P->ps.max_prime = c->pre.maxp[t.presieve_groups - 1];
     P->med_lo = prime_count_le(c, P->ps.max_prime);
     P->coop_hi = std::max(P->med_lo, prime_count_le(c, t.coop_max));
+    {
+        // primes whose 60-multiple warp step still fits the tile slice of one warp
+        // are struck by the whole CTA
+        const uint32_t nw = (uint32_t)tile_threads(t.tile_log2) / 32;
+        P->blk_hi = std::max(P->med_lo, std::min(P->coop_hi, prime_count_le(c, (1ull << t.tile_log2) / (60 * nw))));
+    }
     const uint32_t large_lo = std::max(P->med_lo, prime_count_le(c, t.medium_max));
     const uint64_t pool_cap = pool_cap_in ? pool_cap_in : c->scr.pool_entries;
 
@@ -270,8 +327,6 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
         if (!grp_open) return;
         P->groups.push_back(grp);
         ep.ng++;
-        const uint32_t nch = (grp.p_hi - grp.p_lo + kScatterChunk - 1) / kScatterChunk;
-        ep.nchunks = std::max(ep.nchunks, nch);
         grp_open = false;
     };
 
@@ -342,6 +397,7 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     close_epoch();
     if (P->pool_entries > pool_cap) P->pool_entries = pool_cap;
     for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
+    make_chunks(c, P.get());
     return P;
 }
 
@@ -359,6 +415,7 @@ Plan::~Plan()
     if (d_tiles) cudaFree(d_tiles);
     if (d_sus) cudaFree(d_sus);
     if (d_groups) cudaFree(d_groups);
+    if (d_chunks) cudaFree(d_chunks);
 }
 
 template <class T>
@@ -376,6 +433,7 @@ sieve_status upload_plan(sieve_ctx *c, Plan *P, cudaStream_t st)
     sieve_status s = upload_vec(&P->d_tiles, P->tiles, st);
     if (!s) s = upload_vec(&P->d_sus, P->sus, st);
     if (!s) s = upload_vec(&P->d_groups, P->groups, st);
+    if (!s) s = upload_vec(&P->d_chunks, P->chunks, st);
     return s;
 }
 
@@ -409,6 +467,8 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.barrett = c->d_barrett;
             sa.sus = P->d_sus;
             sa.groups = P->d_groups + e.g0;
+            sa.chunks = P->d_chunks + e.c0;
+            sa.ngroups = e.ng;
             sa.tiles = P->d_tiles + e.tile0;
             sa.bkt = scr.d_bkt;
             sa.bkt_cnt = scr.d_bkt_cnt;
@@ -418,7 +478,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.err = scr.d_err;
             sa.tile_log2 = bt;
             prof_mark(c, SIEVE_K_SCATTER, ls, true);
-            CK(launch_scatter(sa, e.nchunks, e.ng, ls));
+            CK(launch_scatter(sa, e.nc, ls));
             prof_mark(c, SIEVE_K_SCATTER, ls, false);
             if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt, e.ntiles, scr.d_acc + 1, ls));
         }
@@ -430,6 +490,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         ta.primes = c->d_primes;
         ta.barrett = c->d_barrett;
         ta.med_lo = P->med_lo;
+        ta.blk_hi = P->blk_hi;
         ta.coop_hi = P->coop_hi;
         ta.pat = c->d_pat;
         ta.ps = P->ps;
@@ -568,6 +629,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         ta.barrett = d_boot_m;
         ta.med_lo = med_lo;
         ta.coop_hi = (uint32_t)(std::upper_bound(boot.begin(), boot.end(), 1u << 13) - boot.begin());
+        ta.blk_hi = std::max(med_lo, (uint32_t)(std::upper_bound(boot.begin(), boot.end(), (uint32_t)(B / (60 * 32))) - boot.begin()));
         ta.pat = c->d_pat;
         ta.ps.ngroups = kMaxPresieveGroups;
         for (int g = 0; g < kMaxPresieveGroups; ++g) {

@@ -11,7 +11,7 @@
 
 namespace gbs {
 
-constexpr uint32_t kInvBlock = 256;  // granularity of the 1/p prefix table
+constexpr uint32_t kInvBlock = 32;  // granularity of the 1/p prefix table
 
 struct PresieveTable {
     std::vector<uint32_t> words;
@@ -29,14 +29,15 @@ struct ReqSpec {
 struct Plan {
     sieve_tuning tune;
     PresieveInfo ps;
-    uint32_t med_lo = 0, coop_hi = 0;
+    uint32_t med_lo = 0, blk_hi = 0, coop_hi = 0;
     std::vector<TileDesc> tiles;
     std::vector<SUDesc> sus;
     std::vector<GroupDesc> groups;
+    std::vector<ChunkDesc> chunks;
     struct Epoch {
         uint32_t tile0, ntiles;  // tiles [tile0, tile0+ntiles)
         uint32_t g0, ng;         // scatter groups [g0, g0+ng)
-        uint32_t nchunks;        // scatter grid x
+        uint32_t c0, nc;         // scatter chunks (one CTA each) [c0, c0+nc)
     };
     std::vector<Epoch> epochs;
     uint64_t pool_entries = 0;
@@ -47,6 +48,7 @@ struct Plan {
     TileDesc *d_tiles = nullptr;
     SUDesc *d_sus = nullptr;
     GroupDesc *d_groups = nullptr;
+    ChunkDesc *d_chunks = nullptr;
     // graph replay
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -41,6 +41,38 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// block-wide exclusive scan of one value per thread (T threads); returns the
+// exclusive prefix, total in *tot
+template <int T>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *tot)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < T / 32 ? s_warp[lane] : 0;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (uint32_t)o) wi += y;
+        }
+        if (lane < T / 32) s_warp[lane] = wi - w;
+        if (lane == T / 32 - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + incl - v;
+    *tot = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // tile kernel
 // ---------------------------------------------------------------------------
@@ -99,14 +131,49 @@ __global__ void __launch_bounds__(T) k_tile(TileArgs a)
         __syncthreads();
 
         // ---- medium primes (Sec. 2.1, Sec. 3.2), wheel of Sec. 3.2.1 ----
+        // A lane strikes the (lane%8)-th admissible multiple of wheel period lane/8
+        // (a period is 15 multiples of p, 8 of them admissible), so a warp covers 4
+        // periods = 60 multiples of p per step.
         const uint32_t js15 = (uint32_t)(d.J % 15u);
-        const uint32_t coop_end = min(a.coop_hi, d.med_hi);
+        const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
         {
-            // warp-cooperative: one prime per warp at a time, lane i strikes the
-            // (i%8)-th admissible multiple of wheel period i/8; 60 steps of p per pass
-            const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
-            for (uint32_t b = a.med_lo + warp * 32u; b < coop_end; b += T) {
+            // smallest primes: every warp takes every prime, but only strikes inside
+            // its own slice of the tile (the work of one prime is spread over the CTA)
+            constexpr uint32_t NW = T / 32;
+            const uint32_t sl = ((len + NW - 1) / NW + 31) & ~31u;
+            const uint32_t S0 = min(len, warp * sl), E0 = min(len, S0 + sl);
+            const uint32_t blk_end = min(a.blk_hi, d.med_hi);
+            for (uint32_t b = a.med_lo; b < blk_end; b += 32) {
                 const uint32_t idx = b + lane;
+                uint32_t p = 0, h = len, s = 0;
+                if (idx < blk_end) {
+                    p = a.primes[idx];
+                    const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
+                    h = hh < len ? (uint32_t)hh : len;
+                }
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
+                    const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
+                    const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
+                    if (hj >= E0) continue;
+                    const uint32_t step = 60u * pj;
+                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
+                    if (pos < S0) pos += (S0 - pos + step - 1) / step * step;
+                    while (pos < E0) {
+                        atomicOr(&sm[pos >> 5], 1u << (pos & 31));
+                        pos += step;
+                    }
+                }
+            }
+        }
+        {
+            // one prime per warp at a time; a warp's 32 primes are dealt round-robin
+            // from the whole range so that the warps' loads even out
+            constexpr uint32_t NW = T / 32;
+            const uint32_t lo = max(a.med_lo, a.blk_hi);
+            const uint32_t coop_end = min(a.coop_hi, d.med_hi);
+            for (uint32_t b = lo; b < coop_end; b += 32 * NW) {
+                const uint32_t idx = b + lane * NW + warp;
                 uint32_t p = 0, h = len, s = 0;
                 if (idx < coop_end) {
                     p = a.primes[idx];
@@ -118,8 +185,7 @@ __global__ void __launch_bounds__(T) k_tile(TileArgs a)
                     const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
                     const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
                     if (hj >= len) continue;
-                    const uint32_t k = lane_base + ((c_cum[sj] >> cum_shift) & 15u);
-                    uint32_t pos = hj + k * pj;
+                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
                     const uint32_t step = 60u * pj;
                     while (pos < len) {
                         atomicOr(&sm[pos >> 5], 1u << (pos & 31));
@@ -129,11 +195,26 @@ __global__ void __launch_bounds__(T) k_tile(TileArgs a)
             }
         }
         {
-            // one prime per thread
-            for (uint32_t idx = max(a.med_lo, a.coop_hi) + tid; idx < d.med_hi; idx += T) {
-                const uint32_t p = a.primes[idx];
+            // one prime per thread, the next prime's loads issued ahead
+            const uint32_t end = d.med_hi;
+            uint32_t idx = max(max(a.med_lo, a.blk_hi), a.coop_hi) + tid;
+            uint32_t pn = 0;
+            uint64_t mn = 0;
+            if (idx < end) {
+                pn = a.primes[idx];
+                mn = a.barrett[idx];
+            }
+            while (idx < end) {
+                const uint32_t p = pn;
+                const uint64_t m = mn;
+                const uint32_t nidx = idx + T;
+                if (nidx < end) {
+                    pn = a.primes[nidx];
+                    mn = a.barrett[nidx];
+                }
+                idx = nidx;
                 uint32_t s;
-                const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
+                const uint64_t hh = first_hit(d.J, js15, p, m, s);
                 if (hh >= len) continue;
                 uint32_t h = (uint32_t)hh;
                 for (;;) {
@@ -247,209 +328,166 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // ---------------------------------------------------------------------------
 // scatter kernel: large primes -> per-tile buckets
 //
-// CTA (chunk, group): up to kScatterChunk consecutive large primes, one scatter
-// group (<= kScatterMaxTiles tiles of one or more requests).  Prime-major: a warp
-// takes 32 primes (one per lane, prime and Barrett constant in registers), walks
-// the group's scatter units, computes each unit's first hit (Lemma lem:q, the p^2
-// start of Sec. 1.4, the wheel of Sec. 3.2.1) and emits every hit of the unit
-// into its own staging buffer in shared memory.  When a warp's buffer is full
-// the CTA flushes: histogram by tile, one atomic reservation per (tile, flush) in
-// the tile's bucket, counting sort in shared memory, and a store pass in which
+// CTA = one chunk: a run of consecutive large primes (cut on the host so that
+// chunks carry similar work), walked through every scatter group of the epoch
+// (a group is <= kScatterMaxTiles tiles of one or more requests).  Prime-major: a
+// warp takes 32 primes (one per lane, prime and Barrett constant in registers),
+// walks the group's scatter units, computes each unit's first hit (Lemma lem:q,
+// the p^2 start of Sec. 1.4, the wheel of Sec. 3.2.1) and emits every hit of the
+// unit into its own staging buffer in shared memory, counting hits per tile as
+// it goes.  When a warp's buffer is full the CTA flushes: block scan of the
+// per-tile counts, one atomic reservation per (tile, flush) in the tile's
+// bucket, each warp counting-sorts its own entries, and a store pass in which
 // consecutive lanes write consecutive bucket slots.  Entries are the hit's bit
 // offset inside its tile (uint32).  A bucket that would overflow its capacity
 // spills to a global backstop list instead.
 // ---------------------------------------------------------------------------
-constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 1024, kScE = kScNW * kScEW;
+constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 512, kScE = kScNW * kScEW;
 constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
-                           (size_t)kScatterMaxTiles * (4 + 4 + 8 + 8) /*hist,start,gb,lim*/;
+                           (size_t)kScatterMaxTiles * (8 + 8 + 8 + 4 + 4) /*tbase,tlim,gb,hist,start*/;
 
-__global__ void __launch_bounds__(kScT, 1) k_scatter(ScatterArgs a)
+__global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    unsigned long long *gb = reinterpret_cast<unsigned long long *>(smraw);
-    unsigned long long *lim = gb + kScatterMaxTiles;
-    uint32_t *buf = reinterpret_cast<uint32_t *>(lim + kScatterMaxTiles);
+    unsigned long long *tbase = reinterpret_cast<unsigned long long *>(smraw);
+    unsigned long long *tlim = tbase + kScatterMaxTiles;
+    unsigned long long *gb = tlim + kScatterMaxTiles;
+    uint32_t *buf = reinterpret_cast<uint32_t *>(gb + kScatterMaxTiles);
     uint32_t *srt = buf + kScE;
     uint32_t *hist = srt + kScE;
     uint32_t *start = hist + kScatterMaxTiles;
-    __shared__ uint32_t wc[kScNW];
-    __shared__ uint32_t s_total;
+    __shared__ uint32_t s_warp[33];
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const GroupDesc g = a.groups[blockIdx.y];
-    const uint32_t lo = g.p_lo + blockIdx.x * kScatterChunk;
-    if (lo >= g.p_hi) return;
-    const uint32_t n = min(kScatterChunk, g.p_hi - lo);
-    const uint32_t nlg = (n + 31) / 32;
+    const ChunkDesc ch = a.chunks[blockIdx.x];
+    const uint32_t lo = ch.p_lo;
     const uint32_t bt = a.tile_log2, Bm = (1u << bt) - 1;
-    const uint32_t su_end = g.su0 + g.nsu;
-
-    uint32_t lg = warp, su = g.su0;
-    bool need_load = true, need_hit = true;
-    uint32_t p = 0, h = kStateInf, s = 0;
-    uint64_t m = 0;
     uint32_t *wb = buf + warp * kScEW;
 
-    for (;;) {
-        // ---- generate into the warp's staging buffer ----
-        uint32_t wcnt = 0;
-        bool full = false;
-        while (lg < nlg) {
-            if (need_load) {
-                const uint32_t idx = lg * 32 + lane;
-                p = idx < n ? a.primes[lo + idx] : 0u;
-                m = idx < n ? a.barrett[lo + idx] : 0ull;
-                need_load = false;
-            }
-            const SUDesc u = a.sus[su];
-            if (need_hit) {
-                h = kStateInf;
-                s = 0;
-                if (p != 0 && p <= u.plimit) {
-                    const uint64_t hh = first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
-                    if (hh < kStateInf) h = (uint32_t)hh;
-                }
-                need_hit = false;
-            }
-            const uint32_t ebase = u.tile_rel << bt;
-            for (;;) {
-                const bool act = h < u.span;
-                const uint32_t mask = __ballot_sync(0xffffffffu, act);
-                if (!mask) break;
-                if (wcnt + 32 > (uint32_t)kScEW) {
-                    full = true;
-                    break;
-                }
-                if (act) {
-                    wb[wcnt + __popc(mask & lanemask_lt())] = ebase + h;
-                    const uint64_t nh = (uint64_t)h + (uint64_t)wheel_gap(s) * p;
-                    h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
-                    s = (s + 1) & 7;
-                }
-                wcnt += __popc(mask);
-            }
-            if (full) break;
-            need_hit = true;
-            if (++su == su_end) {
-                su = g.su0;
-                lg += kScNW;
-                need_load = true;
-            }
+    for (uint32_t gi = 0; gi < a.ngroups; ++gi) {
+        const GroupDesc g = a.groups[gi];
+        if (lo >= min(ch.p_hi, g.p_hi)) continue;
+        const uint32_t n = min(ch.p_hi, g.p_hi) - lo;
+        const uint32_t nlg = (n + 31) / 32;
+        const uint32_t su_end = g.su0 + g.nsu;
+        for (uint32_t k = tid; k < g.ntiles; k += kScT) {
+            const TileDesc &td = a.tiles[g.tile0 + k];
+            tbase[k] = td.bkt_off;
+            tlim[k] = td.bkt_off + td.bkt_cap;
+            hist[k] = 0;
         }
-        if (lane == 0) wc[warp] = wcnt;
-        const bool more = lg < nlg;
-        for (uint32_t k = tid; k < g.ntiles; k += kScT) hist[k] = 0;
         __syncthreads();
 
-        // ---- flush: histogram by tile ----
-        for (uint32_t e = tid; e < (uint32_t)kScE; e += kScT) {
-            if ((e % kScEW) < wc[e / kScEW]) atomicAdd(&hist[buf[e] >> bt], 1u);
-        }
-        __syncthreads();
-        // ---- exclusive scan (one warp) ----
-        if (warp == 0) {
-            const uint32_t per = (g.ntiles + 31) / 32;
-            const uint32_t base = lane * per;
-            uint32_t sum = 0;
-            for (uint32_t j = 0; j < per; ++j)
-                if (base + j < g.ntiles) sum += hist[base + j];
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += y;
-            }
-            uint32_t run = incl - sum;
-            for (uint32_t j = 0; j < per; ++j) {
-                if (base + j < g.ntiles) {
-                    start[base + j] = run;
-                    run += hist[base + j];
+        uint32_t lg = warp, su = g.su0;
+        bool need_load = true, need_hit = true;
+        uint32_t p = 0, h = kStateInf, s = 0;
+        uint64_t m = 0;
+        for (;;) {
+            // ---- generate into the warp's staging buffer, counting per tile ----
+            uint32_t wcnt = 0;
+            bool full = false;
+            while (lg < nlg) {
+                if (need_load) {
+                    const uint32_t idx = lg * 32 + lane;
+                    p = idx < n ? a.primes[lo + idx] : 0u;
+                    m = idx < n ? a.barrett[lo + idx] : 0ull;
+                    need_load = false;
+                }
+                const SUDesc u = a.sus[su];
+                if (need_hit) {
+                    h = kStateInf;
+                    s = 0;
+                    if (p != 0 && p <= u.plimit) {
+                        const uint64_t hh = first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
+                        if (hh < kStateInf) h = (uint32_t)hh;
+                    }
+                    need_hit = false;
+                }
+                const uint32_t ebase = u.tile_rel << bt;
+                for (;;) {
+                    const bool act = h < u.span;
+                    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+                    if (!mask) break;
+                    if (wcnt + 32 > (uint32_t)kScEW) {
+                        full = true;
+                        break;
+                    }
+                    if (act) {
+                        const uint32_t v = ebase + h;
+                        wb[wcnt + __popc(mask & lanemask_lt())] = v;
+                        atomicAdd(&hist[v >> bt], 1u);
+                        const uint64_t nh = (uint64_t)h + (uint64_t)wheel_gap(s) * p;
+                        h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
+                        s = (s + 1) & 7;
+                    }
+                    wcnt += __popc(mask);
+                }
+                if (full) break;
+                need_hit = true;
+                if (++su == su_end) {
+                    su = g.su0;
+                    lg += kScNW;
+                    need_load = true;
                 }
             }
-            if (lane == 31) s_total = incl;
-        }
-        __syncthreads();
-        // ---- one reservation per non-empty tile ----
-        for (uint32_t k = tid; k < g.ntiles; k += kScT) {
-            const uint32_t c = hist[k];
-            if (c) {
-                const TileDesc &td = a.tiles[g.tile0 + k];
-                gb[k] = td.bkt_off + atomicAdd(&a.bkt_cnt[g.tile0 + k], c);
-                lim[k] = td.bkt_off + td.bkt_cap;
+            const bool more = lg < nlg;
+            __syncthreads();
+
+            // ---- flush: scan of the per-tile counts (two counters per thread) ----
+            const uint32_t k0 = 2 * tid;
+            const uint32_t c0 = k0 < g.ntiles ? hist[k0] : 0u, c1 = k0 + 1 < g.ntiles ? hist[k0 + 1] : 0u;
+            uint32_t total;
+            const uint32_t ex = block_excl_scan<kScT>(c0 + c1, s_warp, &total);
+            // one reservation per non-empty tile; the counters become sort cursors
+            if (k0 < g.ntiles) {
+                start[k0] = ex;
+                hist[k0] = ex;
+                if (c0) gb[k0] = tbase[k0] + atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
             }
-            hist[k] = start[k];
-        }
-        __syncthreads();
-        // ---- counting sort into srt ----
-        for (uint32_t e = tid; e < (uint32_t)kScE; e += kScT) {
-            if ((e % kScEW) < wc[e / kScEW]) {
-                const uint32_t v = buf[e];
+            if (k0 + 1 < g.ntiles) {
+                start[k0 + 1] = ex + c0;
+                hist[k0 + 1] = ex + c0;
+                if (c1) gb[k0 + 1] = tbase[k0 + 1] + atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
+            }
+            __syncthreads();
+            // ---- each warp sorts its own entries by tile ----
+            for (uint32_t i = lane; i < wcnt; i += 32) {
+                const uint32_t v = wb[i];
                 srt[atomicAdd(&hist[v >> bt], 1u)] = v;
             }
-        }
-        __syncthreads();
-        // ---- store: consecutive lanes -> consecutive slots of one bucket ----
-        const uint32_t total = s_total;
-        for (uint32_t i = tid; i < total; i += kScT) {
-            const uint32_t v = srt[i];
-            const uint32_t k = v >> bt;
-            const unsigned long long dst = gb[k] + (i - start[k]);
-            const uint32_t off = v & Bm;
-            if (dst < lim[k]) {
-                a.bkt[dst] = off;
-            } else {
-                const uint32_t o = atomicAdd(a.ovf_cnt, 1u);
-                if (o < a.ovf_cap)
-                    a.ovf[o] = ((unsigned long long)(g.tile0 + k) << 32) | off;
-                else
-                    atomicOr(a.err, kErrOverflow);
+            __syncthreads();
+            // ---- store: consecutive lanes -> consecutive slots of one bucket ----
+            for (uint32_t i = tid; i < total; i += kScT) {
+                const uint32_t v = srt[i];
+                const uint32_t k = v >> bt;
+                const unsigned long long dst = gb[k] + (i - start[k]);
+                const uint32_t off = v & Bm;
+                if (dst < tlim[k]) {
+                    a.bkt[dst] = off;
+                } else {
+                    const uint32_t o = atomicAdd(a.ovf_cnt, 1u);
+                    if (o < a.ovf_cap)
+                        a.ovf[o] = ((unsigned long long)(g.tile0 + k) << 32) | off;
+                    else
+                        atomicOr(a.err, kErrOverflow);
+                }
             }
+            // cursors are no longer read: zero the counts for the next round
+            for (uint32_t k = tid; k < g.ntiles; k += kScT) hist[k] = 0;
+            if (!__syncthreads_or(more)) break;
         }
-        if (!__syncthreads_or(more)) break;
     }
 }
 
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, uint32_t ngroups, cudaStream_t st)
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, cudaStream_t st)
 {
-    k_scatter<<<dim3(nchunks, ngroups), kScT, kScSmem, st>>>(a);
+    k_scatter<<<nchunks, kScT, kScSmem, st>>>(a);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // base of Sec. 1.4 on the device
 // ---------------------------------------------------------------------------
-// block-wide exclusive scan of one value per thread (T threads); returns the
-// exclusive prefix, total in *tot
-template <int T>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *tot)
-{
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < T / 32 ? s_warp[lane] : 0;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= (uint32_t)o) wi += y;
-        }
-        if (lane < T / 32) s_warp[lane] = wi - w;
-        if (lane == T / 32 - 1) s_warp[32] = wi;
-    }
-    __syncthreads();
-    const uint32_t r = s_warp[warp] + incl - v;
-    *tot = s_warp[32];
-    __syncthreads();
-    return r;
-}
-
 // odd primes below 2^17 (index j < 2^16 stands for 2j+1), one CTA: striking with
 // every odd d <= 361 = floor(sqrt(131071)) from d^2 on (Sec. 1.1, Sec. 1.4)
 __global__ void __launch_bounds__(1024) k_bootstrap(uint32_t *primes_out, uint32_t *count_out)

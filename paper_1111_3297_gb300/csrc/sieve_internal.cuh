@@ -168,6 +168,10 @@ struct GroupDesc {      // scatter units sharing one flush domain (<= kScatterMa
     uint32_t p_lo, p_hi;     // large primes: base indices [p_lo, p_hi)
 };
 
+struct ChunkDesc {      // one scatter CTA: large primes [p_lo, p_hi), through all groups of the epoch
+    uint32_t p_lo, p_hi;
+};
+
 constexpr uint32_t kStateInf = 0xFFFFFFFFu;
 
 // device error bits
@@ -180,7 +184,9 @@ struct TileArgs {
     uint32_t *work;                 // persistent-grid work counter (zeroed before launch)
     const uint32_t *primes;
     const uint64_t *barrett;
-    uint32_t med_lo, coop_hi;       // medium primes start at med_lo; warp-cooperative below coop_hi
+    uint32_t med_lo, blk_hi, coop_hi;  // medium primes start at med_lo; [med_lo, blk_hi) struck by
+                                       // the whole CTA (each warp its slice), [blk_hi, coop_hi) one
+                                       // warp per prime, the rest one thread per prime
     const uint32_t *pat;
     PresieveInfo ps;
     const uint32_t *bkt;            // bucket pool
@@ -198,6 +204,8 @@ struct ScatterArgs {
     const uint64_t *barrett;
     const SUDesc *sus;
     const GroupDesc *groups;
+    const ChunkDesc *chunks;        // one per CTA
+    uint32_t ngroups;               // groups of the epoch
     const TileDesc *tiles;          // bucket offset and capacity of every tile
     uint32_t *bkt;
     uint32_t *bkt_cnt;
@@ -213,9 +221,8 @@ int tile_threads(uint32_t tile_log2);
 int tile_blocks_per_sm(uint32_t tile_log2);
 size_t tile_smem_bytes(uint32_t tile_log2);
 cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
-constexpr uint32_t kScatterChunk = 16384;    // primes per scatter CTA
 constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, uint32_t ngroups, cudaStream_t st);
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, cudaStream_t st);
 cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
 cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
                            uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out,
