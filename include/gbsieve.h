@@ -53,7 +53,8 @@ const char *sieve_strerror(sieve_status s);
  * largest number is <= max_v.  Builds the base of Sec. 1.4 (Definition "base":
  * the odd primes p <= sqrt(max_v)) on the device and keeps it resident with one
  * 64-bit reduction constant per prime.  mem_budget bounds the device memory the
- * context uses for large-prime buckets (0 = 8 GiB).  Waits for the device.
+ * context uses for large-prime buckets (0 = 16 GiB, split into two pools).
+ * Waits for the device.
  * On success *ctx owns all its device memory until sieve_destroy.
  */
 sieve_status sieve_init(sieve_ctx **ctx, int device, uint64_t max_v, size_t mem_budget);

@@ -53,6 +53,7 @@ void build_presieve(PresieveTable &t)
         t.modulus[g] = P;
         t.maxp[g] = maxp;
         t.word_off[g] = (uint32_t)t.words.size();
+        // 32-bit words covering bits 0 .. P+63, then overlapping 64-bit windows
         const uint32_t nw = (P + 64 + 31) / 32 + 1;
         std::vector<uint32_t> w(nw, 0);
         for (uint32_t rho = 0; rho < 32 * nw; ++rho) {
@@ -62,7 +63,7 @@ void build_presieve(PresieveTable &t)
                 if ((2 * (uint64_t)r + 1) % kGroups[g][i] == 0) hit = true;
             if (hit) w[rho / 32] |= 1u << (rho % 32);
         }
-        t.words.insert(t.words.end(), w.begin(), w.end());
+        for (uint32_t i = 0; i + 1 < nw; ++i) t.words.push_back((unsigned long long)w[i] | ((unsigned long long)w[i + 1] << 32));
     }
 }
 
@@ -180,28 +181,51 @@ sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap)
     sieve_status r = alloc_dev((void **)&s.d_small, 64);
     if (!r) r = alloc_dev((void **)&s.d_err, 16);
     if (!r) r = alloc_dev((void **)&s.d_acc, 64);
-    if (!r) r = alloc_dev((void **)&s.d_ovf, (size_t)ovf_cap * 8);
+    if (!r) r = alloc_dev((void **)&s.d_ovf[0], (size_t)ovf_cap * 8);
+    if (!r) r = alloc_dev((void **)&s.d_ovf[1], (size_t)ovf_cap * 8);
     if (r) return r;
     CK(cudaMemset(s.d_small, 0, 64));
     CK(cudaMemset(s.d_err, 0, 16));
     CK(cudaMemset(s.d_acc, 0, 64));
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&s.s_tile, cudaStreamNonBlocking, greatest));
+    CK(cudaStreamCreateWithPriority(&s.s_scat, cudaStreamNonBlocking, least));
+    CK(cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&s.ev_scat[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&s.ev_tile[b], cudaEventDisableTiming));
+    }
     return SIEVE_OK;
 }
 
 void scratch_free(Scratch &s)
 {
-    for (void *p : {(void *)s.d_bkt, (void *)s.d_bkt_cnt, (void *)s.d_ovf, (void *)s.d_small, (void *)s.d_err,
-                    (void *)s.d_acc})
+    if (s.s_tile) cudaStreamSynchronize(s.s_tile);
+    if (s.s_scat) cudaStreamSynchronize(s.s_scat);
+    for (int b = 0; b < 2; ++b)
+        for (void *p : {(void *)s.d_bkt[b], (void *)s.d_bkt_cnt[b], (void *)s.d_ovf[b]})
+            if (p) cudaFree(p);
+    for (void *p : {(void *)s.d_small, (void *)s.d_err, (void *)s.d_acc})
         if (p) cudaFree(p);
+    if (s.s_tile) cudaStreamDestroy(s.s_tile);
+    if (s.s_scat) cudaStreamDestroy(s.s_scat);
+    for (cudaEvent_t e : {s.ev_fork, s.ev_join, s.ev_scat[0], s.ev_scat[1], s.ev_tile[0], s.ev_tile[1]})
+        if (e) cudaEventDestroy(e);
     s = Scratch{};
 }
 
 sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles)
 {
     if (pool_entries > s.pool_entries) return SIEVE_ENOMEM;
-    sieve_status r = ensure((void **)&s.d_bkt, &s.bkt_bytes, (size_t)pool_entries * 4 + 64, &s.gen);
-    if (r) return r;
-    return ensure((void **)&s.d_bkt_cnt, &s.bkt_cnt_bytes, (size_t)max_epoch_tiles * 4 + 64, &s.gen);
+    for (int b = 0; b < 2; ++b) {
+        sieve_status r = ensure((void **)&s.d_bkt[b], &s.bkt_bytes[b], (size_t)pool_entries * 4 + 64, &s.gen);
+        if (r) return r;
+        r = ensure((void **)&s.d_bkt_cnt[b], &s.bkt_cnt_bytes[b], (size_t)max_epoch_tiles * 4 + 64, &s.gen);
+        if (r) return r;
+    }
+    return SIEVE_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -273,6 +297,9 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     for (int g = 0; g < kMaxPresieveGroups; ++g) {
         P->ps.modulus[g] = c->pre.modulus[g];
         P->ps.word_off[g] = c->pre.word_off[g];
+        P->ps.barrett[g] = 0xFFFFFFFFFFFFFFFFull / c->pre.modulus[g];
+        P->ps.inc[g] = (uint32_t)((32ull * tile_threads(t.tile_log2)) % c->pre.modulus[g]);
+        P->ps.inv[g] = 1.0f / (float)c->pre.modulus[g];
     }
     P->ps.max_prime = c->pre.maxp[t.presieve_groups - 1];
     P->med_lo = prime_count_le(c, P->ps.max_prime);
@@ -452,16 +479,28 @@ static void prof_mark(sieve_ctx *c, int kind, cudaStream_t st, bool begin)
     }
 }
 
+// The launch sequence of a plan.  The caller's stream forks into the scratch's
+// tile stream (high priority) and scatter stream (low priority) and joins them
+// at the end.  Epoch e uses bucket pool e%2: its scatter runs on the scatter
+// stream as soon as the tile launch of epoch e-2 has drained that pool, so the
+// scatter of epoch e+1 overlaps the tile launch of epoch e.
 sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, unsigned long long *counts,
                           uint32_t ncounts, cudaStream_t ls)
 {
     const uint32_t bt = P->tune.tile_log2;
-    if (counts && ncounts) CK(cudaMemsetAsync(counts, 0, (size_t)ncounts * 8, ls));
     const uint32_t tgrid_max = (uint32_t)(c->nsm * tile_blocks_per_sm(bt));
-    for (const Plan::Epoch &e : P->epochs) {
+    cudaStream_t st = scr.s_tile, ss = scr.s_scat;
+    CK(cudaEventRecord(scr.ev_fork, ls));
+    CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
+    CK(cudaStreamWaitEvent(ss, scr.ev_fork, 0));
+    if (counts && ncounts) CK(cudaMemsetAsync(counts, 0, (size_t)ncounts * 8, st));
+    for (size_t ei = 0; ei < P->epochs.size(); ++ei) {
+        const Plan::Epoch &e = P->epochs[ei];
+        const int b = (int)(ei & 1);
         if (e.ng) {
-            CK(cudaMemsetAsync(scr.d_bkt_cnt, 0, (size_t)e.ntiles * 4, ls));
-            CK(cudaMemsetAsync(scr.d_small + 1, 0, 4, ls));
+            if (ei >= 2) CK(cudaStreamWaitEvent(ss, scr.ev_tile[b], 0));
+            CK(cudaMemsetAsync(scr.d_bkt_cnt[b], 0, (size_t)e.ntiles * 4, ss));
+            CK(cudaMemsetAsync(scr.d_small + 2 + b, 0, 4, ss));
             ScatterArgs sa;
             sa.primes = c->d_primes;
             sa.barrett = c->d_barrett;
@@ -470,19 +509,21 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.chunks = P->d_chunks + e.c0;
             sa.ngroups = e.ng;
             sa.tiles = P->d_tiles + e.tile0;
-            sa.bkt = scr.d_bkt;
-            sa.bkt_cnt = scr.d_bkt_cnt;
-            sa.ovf = scr.d_ovf;
-            sa.ovf_cnt = scr.d_small + 1;
+            sa.bkt = scr.d_bkt[b];
+            sa.bkt_cnt = scr.d_bkt_cnt[b];
+            sa.ovf = scr.d_ovf[b];
+            sa.ovf_cnt = scr.d_small + 2 + b;
             sa.ovf_cap = scr.ovf_cap;
             sa.err = scr.d_err;
             sa.tile_log2 = bt;
-            prof_mark(c, SIEVE_K_SCATTER, ls, true);
-            CK(launch_scatter(sa, e.nc, ls));
-            prof_mark(c, SIEVE_K_SCATTER, ls, false);
-            if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt, e.ntiles, scr.d_acc + 1, ls));
+            prof_mark(c, SIEVE_K_SCATTER, ss, true);
+            CK(launch_scatter(sa, e.nc, ss));
+            prof_mark(c, SIEVE_K_SCATTER, ss, false);
+            if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt[b], e.ntiles, scr.d_acc + 1, ss));
+            CK(cudaEventRecord(scr.ev_scat[b], ss));
+            CK(cudaStreamWaitEvent(st, scr.ev_scat[b], 0));
         }
-        CK(cudaMemsetAsync(scr.d_small, 0, 4, ls));
+        CK(cudaMemsetAsync(scr.d_small, 0, 4, st));
         TileArgs ta;
         ta.tiles = P->d_tiles + e.tile0;
         ta.ntiles = e.ntiles;
@@ -494,18 +535,23 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         ta.coop_hi = P->coop_hi;
         ta.pat = c->d_pat;
         ta.ps = P->ps;
-        ta.bkt = scr.d_bkt;
-        ta.bkt_cnt = scr.d_bkt_cnt;
-        ta.ovf = scr.d_ovf;
-        ta.ovf_cnt = scr.d_small + 1;
+        ta.bkt = scr.d_bkt[b];
+        ta.bkt_cnt = scr.d_bkt_cnt[b];
+        ta.ovf = scr.d_ovf[b];
+        ta.ovf_cnt = scr.d_small + 2 + b;
         ta.ovf_cap = scr.ovf_cap;
         ta.out = out;
         ta.req_counts = counts;
         ta.tile_log2 = bt;
-        prof_mark(c, SIEVE_K_TILE, ls, true);
-        CK(launch_tiles(ta, std::min<uint32_t>(e.ntiles, tgrid_max), ls));
-        prof_mark(c, SIEVE_K_TILE, ls, false);
+        prof_mark(c, SIEVE_K_TILE, st, true);
+        CK(launch_tiles(ta, std::min<uint32_t>(e.ntiles, tgrid_max), st));
+        prof_mark(c, SIEVE_K_TILE, st, false);
+        CK(cudaEventRecord(scr.ev_tile[b], st));
     }
+    CK(cudaEventRecord(scr.ev_join, ss));
+    CK(cudaStreamWaitEvent(st, scr.ev_join, 0));
+    CK(cudaEventRecord(scr.ev_join, st));
+    CK(cudaStreamWaitEvent(ls, scr.ev_join, 0));
     if (c->prof) {
         c->prof_acc.tiles += P->tiles.size();
         c->prof_acc.bits += P->bits;
@@ -635,9 +681,12 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         for (int g = 0; g < kMaxPresieveGroups; ++g) {
             ta.ps.modulus[g] = c->pre.modulus[g];
             ta.ps.word_off[g] = c->pre.word_off[g];
+            ta.ps.barrett[g] = 0xFFFFFFFFFFFFFFFFull / c->pre.modulus[g];
+            ta.ps.inc[g] = (uint32_t)((32ull * tile_threads(bt)) % c->pre.modulus[g]);
+            ta.ps.inv[g] = 1.0f / (float)c->pre.modulus[g];
         }
         ta.ps.max_prime = c->pre.maxp[kMaxPresieveGroups - 1];
-        ta.ovf_cnt = c->scr.d_small + 1;
+        ta.ovf_cnt = c->scr.d_small + 2;
         ta.out = d_tab;
         ta.tile_log2 = bt;
         CK(cudaMemsetAsync(c->scr.d_small, 0, 8, st));
@@ -694,15 +743,15 @@ sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_
     CK(set_kernel_attributes());
     c->max_v = max_v;
     c->base_limit = std::min<uint64_t>(isqrt_u64(max_v), 0xFFFFFFFFull);
-    c->mem_budget = mem_budget ? mem_budget : (size_t)8 << 30;
+    c->mem_budget = mem_budget ? mem_budget : (size_t)16 << 30;
     build_presieve(c->pre);
-    sieve_status s = alloc_dev((void **)&c->d_pat, c->pre.words.size() * 4);
-    if (!s) s = scratch_init(c->scr, c->mem_budget / 4, 1u << 22);
+    sieve_status s = alloc_dev((void **)&c->d_pat, c->pre.words.size() * 8);
+    if (!s) s = scratch_init(c->scr, c->mem_budget / 8, 1u << 22);  // two pools
     if (s) {
         sieve_destroy(c.release());
         return s;
     }
-    CK(cudaMemcpy(c->d_pat, c->pre.words.data(), c->pre.words.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_pat, c->pre.words.data(), c->pre.words.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMallocHost((void **)&c->h_acc, 64));
     CK(cudaMallocHost((void **)&c->h_err, 16));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));

@@ -14,7 +14,7 @@ namespace gbs {
 constexpr uint32_t kInvBlock = 32;  // granularity of the 1/p prefix table
 
 struct PresieveTable {
-    std::vector<uint32_t> words;
+    std::vector<unsigned long long> words;  // overlapping 64-bit windows
     uint32_t modulus[kMaxPresieveGroups];
     uint32_t word_off[kMaxPresieveGroups];
     uint32_t maxp[kMaxPresieveGroups];
@@ -67,17 +67,22 @@ struct ProfRec {
 // device scratch of one launch sequence in flight (the context owns one; each
 // serving lane owns its own so that batches on different streams never share)
 struct Scratch {
-    uint32_t *d_bkt = nullptr;  // large-prime bucket pool
-    size_t bkt_bytes = 0;
-    uint32_t *d_bkt_cnt = nullptr;  // entries per tile of the current epoch
-    size_t bkt_cnt_bytes = 0;
-    unsigned long long *d_ovf = nullptr;  // overflow backstop list
+    // two bucket pools: the scatter of epoch e+1 fills one while the tile
+    // kernel of epoch e drains the other
+    uint32_t *d_bkt[2] = {nullptr, nullptr};
+    size_t bkt_bytes[2] = {0, 0};
+    uint32_t *d_bkt_cnt[2] = {nullptr, nullptr};  // entries per tile of the pool's epoch
+    size_t bkt_cnt_bytes[2] = {0, 0};
+    unsigned long long *d_ovf[2] = {nullptr, nullptr};  // overflow backstop lists
     uint32_t ovf_cap = 0;
-    uint32_t *d_small = nullptr;  // [0] tile work counter, [1] overflow count
+    uint32_t *d_small = nullptr;  // [0] tile work counter, [2+b] overflow count of pool b
     int *d_err = nullptr;         // device error bits
     unsigned long long *d_acc = nullptr;  // [0] popcount, [1] profiled hits
     uint64_t gen = 0;             // bumped when a buffer moves (captured graphs re-capture)
-    uint64_t pool_entries = 0;    // bucket pool capacity allowed (entries)
+    uint64_t pool_entries = 0;    // capacity allowed per pool (entries)
+    cudaStream_t s_tile = nullptr, s_scat = nullptr;  // high / low priority
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_scat[2] = {nullptr, nullptr},
+                ev_tile[2] = {nullptr, nullptr};
 };
 sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap);
 void scratch_free(Scratch &s);
@@ -93,7 +98,7 @@ struct sieve_ctx {
     std::vector<uint32_t> h_primes;
     std::vector<double> h_inv_prefix;  // sum of 1/p over the first k*kInvBlock primes
     gbs::PresieveTable pre;
-    uint32_t *d_pat = nullptr;
+    unsigned long long *d_pat = nullptr;
     sieve_tuning tune[SIEVE_TUNE_CLASSES];
     size_t mem_budget = 0;
     gbs::Scratch scr;

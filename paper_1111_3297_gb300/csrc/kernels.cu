@@ -77,7 +77,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
 // tile kernel
 // ---------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(T) k_tile(TileArgs a)
+__global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_tile;
@@ -95,36 +95,47 @@ __global__ void __launch_bounds__(T) k_tile(TileArgs a)
         const uint32_t len = d.len, nwords = len >> 5;
 
         // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
-        if (tid < ng) s_rho0[tid] = (uint32_t)(d.J % a.ps.modulus[tid]);
+        // Two passes of up to 7 groups each (fewer live residues); the second
+        // pass ORs into the words the first one wrote.
+        if (tid < ng) s_rho0[tid] = mod_barrett(d.J, a.ps.modulus[tid], a.ps.barrett[tid]);
         __syncthreads();
-        {
-            uint32_t rho[kMaxPresieveGroups], inc[kMaxPresieveGroups];
+        constexpr int kPass = 7;
+#pragma unroll 1
+        for (int g0 = 0; g0 < (int)ng; g0 += kPass) {
+            uint32_t rho[kPass];
 #pragma unroll
-            for (int g = 0; g < kMaxPresieveGroups; ++g) {
+            for (int k = 0; k < kPass; ++k) {
+                const int g = g0 + k;
+                rho[k] = 0;
                 if (g < (int)ng) {
-                    const uint32_t P = a.ps.modulus[g];
-                    rho[g] = (s_rho0[g] + 32u * tid) % P;
-                    inc[g] = (32u * T) % P;
-                } else {
-                    rho[g] = 0;
-                    inc[g] = 0;
+                    // thread tid starts at word tid: rho = (rho0 + 32 tid) mod P, the
+                    // quotient estimated in float and corrected exactly
+                    const uint32_t P = a.ps.modulus[g], x = 32u * tid;
+                    const uint32_t q = __float2uint_rz(__uint2float_rn(x) * a.ps.inv[g]);
+                    int32_t r = (int32_t)(x - q * P);
+                    if (r < 0) r += (int32_t)P;
+                    if (r >= (int32_t)P) r -= (int32_t)P;
+                    const uint32_t r2 = s_rho0[g] + (uint32_t)r;
+                    rho[k] = r2 >= P ? r2 - P : r2;
                 }
             }
             for (uint32_t w = tid; w < nwords; w += T) {
-                uint32_t mask = 0;
+                uint32_t mask = g0 ? sm[w] : 0u;
 #pragma unroll
-                for (int g = 0; g < kMaxPresieveGroups; ++g) {
+                for (int k = 0; k < kPass; ++k) {
+                    const int g = g0 + k;
                     if (g < (int)ng) {
-                        const uint32_t *pt = a.pat + a.ps.word_off[g];
-                        const uint32_t r = rho[g];
-                        const uint32_t lo = __ldg(pt + (r >> 5)), hi = __ldg(pt + (r >> 5) + 1);
-                        mask |= __funnelshift_r(lo, hi, r & 31);
-                        uint32_t nr = r + inc[g];
-                        rho[g] = nr >= a.ps.modulus[g] ? nr - a.ps.modulus[g] : nr;
+                        const uint32_t r = rho[k];
+                        mask |= (uint32_t)(__ldg(a.pat + a.ps.word_off[g] + (r >> 5)) >> (r & 31));
+                        const uint32_t nr = r + a.ps.inc[g];
+                        rho[k] = nr >= a.ps.modulus[g] ? nr - a.ps.modulus[g] : nr;
                     }
                 }
-                const uint64_t Jw = d.J + 32ull * w;
-                if (Jw < 64) mask &= ~(uint32_t)(kSmallPrimeBits >> Jw);
+                if (g0 + kPass >= (int)ng) {
+                    // last pass: a pattern also marks each small prime q = q*1 itself
+                    const uint64_t Jw = d.J + 32ull * w;
+                    if (Jw < 64) mask &= ~(uint32_t)(kSmallPrimeBits >> Jw);
+                }
                 sm[w] = mask;
             }
         }
@@ -337,14 +348,15 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // unit into its own staging buffer in shared memory, counting hits per tile as
 // it goes.  When a warp's buffer is full the CTA flushes: block scan of the
 // per-tile counts, one atomic reservation per (tile, flush) in the tile's
-// bucket, each warp counting-sorts its own entries, and a store pass in which
+// bucket (issued before the sort, consumed after it), each warp counting-sorts
+// its own entries, and a store pass in which
 // consecutive lanes write consecutive bucket slots.  Entries are the hit's bit
 // offset inside its tile (uint32).  A bucket that would overflow its capacity
 // spills to a global backstop list instead.
 // ---------------------------------------------------------------------------
 constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 512, kScE = kScNW * kScEW;
 constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
-                           (size_t)kScatterMaxTiles * (8 + 8 + 8 + 4 + 4) /*tbase,tlim,gb,hist,start*/;
+                           (size_t)kScatterMaxTiles * (8 + 8 + 8 + 4) /*tbase,tlim,gb,hist*/;
 
 __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
 {
@@ -355,7 +367,6 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
     uint32_t *buf = reinterpret_cast<uint32_t *>(gb + kScatterMaxTiles);
     uint32_t *srt = buf + kScE;
     uint32_t *hist = srt + kScE;
-    uint32_t *start = hist + kScatterMaxTiles;
     __shared__ uint32_t s_warp[33];
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -438,16 +449,16 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
             const uint32_t c0 = k0 < g.ntiles ? hist[k0] : 0u, c1 = k0 + 1 < g.ntiles ? hist[k0 + 1] : 0u;
             uint32_t total;
             const uint32_t ex = block_excl_scan<kScT>(c0 + c1, s_warp, &total);
-            // one reservation per non-empty tile; the counters become sort cursors
+            // the counters become sort cursors; one bucket reservation per non-empty
+            // tile is issued now and its result consumed after the sort
+            uint32_t r0 = 0, r1 = 0;
             if (k0 < g.ntiles) {
-                start[k0] = ex;
                 hist[k0] = ex;
-                if (c0) gb[k0] = tbase[k0] + atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
+                if (c0) r0 = atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
             }
             if (k0 + 1 < g.ntiles) {
-                start[k0 + 1] = ex + c0;
                 hist[k0 + 1] = ex + c0;
-                if (c1) gb[k0 + 1] = tbase[k0 + 1] + atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
+                if (c1) r1 = atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
             }
             __syncthreads();
             // ---- each warp sorts its own entries by tile ----
@@ -455,12 +466,15 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                 const uint32_t v = wb[i];
                 srt[atomicAdd(&hist[v >> bt], 1u)] = v;
             }
+            // sorted position i of tile k goes to bucket slot gb[k] + i
+            if (c0) gb[k0] = tbase[k0] + r0 - ex;
+            if (c1) gb[k0 + 1] = tbase[k0 + 1] + r1 - (ex + c0);
             __syncthreads();
             // ---- store: consecutive lanes -> consecutive slots of one bucket ----
             for (uint32_t i = tid; i < total; i += kScT) {
                 const uint32_t v = srt[i];
                 const uint32_t k = v >> bt;
-                const unsigned long long dst = gb[k] + (i - start[k]);
+                const unsigned long long dst = gb[k] + i;
                 const uint32_t off = v & Bm;
                 if (dst < tlim[k]) {
                     a.bkt[dst] = off;

@@ -251,7 +251,7 @@ sieve_status sieve_server_create(sieve_ctx *c, size_t mem_cap, uint32_t max_infl
             return SIEVE_ENOMEM;
         }
         *L.h_err = 0;
-        if (scratch_init(L.scr, lane_pool / 4, 1u << 20) != SIEVE_OK) {
+        if (scratch_init(L.scr, lane_pool / 8, 1u << 20) != SIEVE_OK) {
             sieve_server_destroy(S.release());
             return SIEVE_ENOMEM;
         }

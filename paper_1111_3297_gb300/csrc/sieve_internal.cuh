@@ -128,15 +128,19 @@ __device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32
 // Pre-sieve (Sec. 3.1): small primes are applied as periodic bit patterns.
 // Group g covers the primes whose product is P_g; bit rho (0 <= rho < P_g + 64)
 // of its pattern is 1 when some prime p of the group divides 2*rho+1 (rho = J
-// mod P_g).  A 32-bit window starting at rho is read with two loads and a
-// funnel shift.
+// mod P_g).  The pattern is stored as overlapping 64-bit words (word i holds
+// bits 32i .. 32i+63), so the 32-bit window starting at rho is one load and one
+// shift.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPresieveGroups = 13;
 struct PresieveInfo {
     uint32_t ngroups;                       // groups applied (1..13)
     uint32_t modulus[kMaxPresieveGroups];   // P_g
-    uint32_t word_off[kMaxPresieveGroups];  // offset of the group's pattern in the table
+    uint32_t word_off[kMaxPresieveGroups];  // offset of the group's pattern (64-bit words)
     uint32_t max_prime;                     // largest prime covered by the applied groups
+    uint64_t barrett[kMaxPresieveGroups];   // floor((2^64-1)/P_g)
+    uint32_t inc[kMaxPresieveGroups];       // (32 * threads per CTA) mod P_g
+    float inv[kMaxPresieveGroups];          // 1/P_g (quotient estimate, corrected exactly)
 };
 
 // ---------------------------------------------------------------------------
@@ -187,7 +191,7 @@ struct TileArgs {
     uint32_t med_lo, blk_hi, coop_hi;  // medium primes start at med_lo; [med_lo, blk_hi) struck by
                                        // the whole CTA (each warp its slice), [blk_hi, coop_hi) one
                                        // warp per prime, the rest one thread per prime
-    const uint32_t *pat;
+    const unsigned long long *pat;
     PresieveInfo ps;
     const uint32_t *bkt;            // bucket pool
     const uint32_t *bkt_cnt;        // entries per tile (indexed like tiles)
