@@ -67,6 +67,47 @@ void build_presieve(PresieveTable &t)
     }
 }
 
+// Tables of the mod-15015 wheel for large primes: the admissible residues of c
+// (odd multiplier, p*c struck only when gcd(c, 15015) = 1) in the order in which
+// stepping c -> c+2 visits them, starting from c = 1.
+void build_big_wheel(std::vector<uint32_t> &gapw, std::vector<uint32_t> &rstate, std::vector<uint16_t> &inv)
+{
+    const uint32_t W = kBigW;
+    auto coprime = [](uint32_t r) { return r % 3 && r % 5 && r % 7 && r % 11 && r % 13; };
+    std::vector<int> pos(W, -1);
+    std::vector<uint32_t> gap;
+    uint32_t r = 1;
+    do {
+        pos[r] = (int)gap.size();
+        uint32_t k = 1;
+        while (!coprime((r + 2 * k) % W)) ++k;
+        gap.push_back(k);
+        r = (r + 2 * k) % W;
+    } while (r != 1);
+    gapw.assign(gap.size() / 8, 0);
+    for (size_t i = 0; i < gap.size(); ++i) gapw[i / 8] |= gap[i] << (4 * (i % 8));
+    rstate.assign(W, 0);
+    for (uint32_t x = 0; x < W; ++x) {
+        uint32_t k = 0;
+        while (!coprime((x + 2 * k) % W)) ++k;
+        rstate[x] = (k << 16) | (uint32_t)pos[(x + 2 * k) % W];
+    }
+    inv.assign(W, 0);
+    for (uint32_t x = 1; x < W; ++x) {
+        if (!coprime(x)) continue;
+        // extended Euclid: t*x = 1 (mod W)
+        int64_t a = x, b = W, t0 = 1, t1 = 0;
+        while (b) {
+            const int64_t q = a / b, ta = a - q * b, tt = t0 - q * t1;
+            a = b;
+            b = ta;
+            t0 = t1;
+            t1 = tt;
+        }
+        inv[x] = (uint16_t)((t0 % (int64_t)W + W) % W);
+    }
+}
+
 }  // namespace gbs
 
 // ---------------------------------------------------------------------------
@@ -207,6 +248,9 @@ void scratch_free(Scratch &s)
     for (int b = 0; b < 2; ++b)
         for (void *p : {(void *)s.d_bkt[b], (void *)s.d_bkt_cnt[b], (void *)s.d_ovf[b]})
             if (p) cudaFree(p);
+    if (s.d_carry) cudaFree(s.d_carry);
+    if (s.d_tcarry_h) cudaFree(s.d_tcarry_h);
+    if (s.d_tcarry_s) cudaFree(s.d_tcarry_s);
     for (void *p : {(void *)s.d_small, (void *)s.d_err, (void *)s.d_acc})
         if (p) cudaFree(p);
     if (s.s_tile) cudaStreamDestroy(s.s_tile);
@@ -216,9 +260,19 @@ void scratch_free(Scratch &s)
     s = Scratch{};
 }
 
-sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles)
+sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles, uint64_t carry_entries,
+                            uint64_t tile_carry_entries)
 {
     if (pool_entries > s.pool_entries) return SIEVE_ENOMEM;
+    if (tile_carry_entries) {
+        sieve_status r = ensure((void **)&s.d_tcarry_h, &s.tcarry_h_bytes, (size_t)tile_carry_entries * 4, &s.gen);
+        if (!r) r = ensure((void **)&s.d_tcarry_s, &s.tcarry_s_bytes, (size_t)tile_carry_entries, &s.gen);
+        if (r) return r;
+    }
+    if (carry_entries) {
+        sieve_status r = ensure((void **)&s.d_carry, &s.carry_bytes, (size_t)carry_entries * 8, &s.gen);
+        if (r) return r;
+    }
     for (int b = 0; b < 2; ++b) {
         sieve_status r = ensure((void **)&s.d_bkt[b], &s.bkt_bytes[b], (size_t)pool_entries * 4 + 64, &s.gen);
         if (r) return r;
@@ -263,7 +317,8 @@ static void make_chunks(sieve_ctx *c, Plan *P)
                 const GroupDesc &G = P->groups[e.g0 + g];
                 const uint32_t a = std::max(i, G.p_lo), b = std::min(j, G.p_hi);
                 if (a >= b) continue;
-                x += kFirstHitCost * G.nsu * (double)(b - a) + span[g] * (8.0 / 15.0) * inv_sum(c, a, b);
+                x += kFirstHitCost * G.nsu * (double)(b - a) +
+                     span[g] * (P->big_wheel ? kBigDensity : 8.0 / 15.0) * inv_sum(c, a, b);
             }
             return x;
         };
@@ -333,6 +388,21 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
                               : 0;
     }
 
+    // Wheel of the large primes: the mod-15015 wheel emits 28% fewer hits than
+    // the mod-15 one but its first hit costs two table reads; it pays when a
+    // prime has hits in most of the units it visits (long intervals).
+    {
+        double hits = 0, visits = 0;
+        for (size_t r = 0; r < reqs.size(); ++r) {
+            if (info[r].large_hi <= large_lo) continue;
+            hits += (double)reqs[r].nbits * info[r].inv;
+            const double units = std::ceil((double)reqs[r].nbits / ((double)t.window_tiles * B));
+            visits += units * (double)(info[r].large_hi - large_lo);
+        }
+        P->big_wheel = visits > 0 && hits >= 1.0 * visits;
+    }
+    const double density = P->big_wheel ? kBigDensity : 8.0 / 15.0;
+
     // tiles in request order; epochs cut at group boundaries
     Plan::Epoch ep{};
     uint64_t ep_pool = 0;
@@ -372,7 +442,7 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
             d.med_hi = ri.med_hi;
             uint32_t cap = 0;
             if (large) {
-                const double e = (double)d.len * (8.0 / 15.0) * ri.inv;
+                const double e = (double)d.len * density * ri.inv;
                 cap = (uint32_t)std::ceil(1.05 * e + 8.0 * std::sqrt(e) + 64.0) + ri.nsmall_large;
                 cap = (cap + 3) & ~3u;
             }
@@ -416,7 +486,7 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
                 }
                 grp.ntiles = rel + 1;
                 grp.p_hi = std::max(grp.p_hi, ri.large_hi);
-                P->exp_large_hits += (double)d.len * (8.0 / 15.0) * ri.inv;
+                P->exp_large_hits += (double)d.len * density * ri.inv;
             }
         }
     }
@@ -425,6 +495,27 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     if (P->pool_entries > pool_cap) P->pool_entries = pool_cap;
     for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
     make_chunks(c, P.get());
+    P->single_request = reqs.size() == 1;
+    {
+        const uint32_t lane_lo = std::max(std::max(P->med_lo, P->blk_hi), P->coop_hi);
+        for (const ReqInfo &ri : info) P->lane_stride = std::max(P->lane_stride, ri.med_hi > lane_lo ? ri.med_hi - lane_lo : 0u);
+    }
+    // carry each prime's next hit from a group to the next when the next group
+    // starts exactly where this one's last unit ends (same request) and both
+    // cover the same primes (then every CTA walks both with the same primes)
+    for (Plan::Epoch &e : P->epochs) {
+        e.carry_base = ~0u;
+        for (uint32_t g = 0; g < e.ng; ++g) e.carry_base = std::min(e.carry_base, P->groups[e.g0 + g].p_lo);
+        for (uint32_t g = 0; g + 1 < e.ng; ++g) {
+            GroupDesc &A = P->groups[e.g0 + g], &B = P->groups[e.g0 + g + 1];
+            const SUDesc &ua = P->sus[A.su0 + A.nsu - 1], &ub = P->sus[B.su0];
+            if (ua.J + ua.span == ub.J && ua.plimit == ub.plimit && A.p_lo == B.p_lo && A.p_hi == B.p_hi) {
+                A.carry_out = 1;
+                B.carry_in = 1;
+                P->carry_entries = std::max<uint64_t>(P->carry_entries, A.p_hi - e.carry_base);
+            }
+        }
+    }
     return P;
 }
 
@@ -509,6 +600,11 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.chunks = P->d_chunks + e.c0;
             sa.ngroups = e.ng;
             sa.tiles = P->d_tiles + e.tile0;
+            sa.carry = scr.d_carry;
+            sa.carry_base = e.carry_base;
+            sa.wheel.gapw = c->d_gapw;
+            sa.wheel.rstate = c->d_rstate;
+            sa.wheel.inv = c->d_winv;
             sa.bkt = scr.d_bkt[b];
             sa.bkt_cnt = scr.d_bkt_cnt[b];
             sa.ovf = scr.d_ovf[b];
@@ -517,7 +613,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.err = scr.d_err;
             sa.tile_log2 = bt;
             prof_mark(c, SIEVE_K_SCATTER, ss, true);
-            CK(launch_scatter(sa, e.nc, ss));
+            CK(launch_scatter(sa, e.nc, P->big_wheel, ss));
             prof_mark(c, SIEVE_K_SCATTER, ss, false);
             if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt[b], e.ntiles, scr.d_acc + 1, ss));
             CK(cudaEventRecord(scr.ev_scat[b], ss));
@@ -543,8 +639,18 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         ta.out = out;
         ta.req_counts = counts;
         ta.tile_log2 = bt;
+        const uint32_t tgrid = std::min<uint32_t>(e.ntiles, tgrid_max);
+        ta.run = 0;
+        ta.carry_h = scr.d_tcarry_h;
+        ta.carry_s = scr.d_tcarry_s;
+        ta.carry_stride = P->lane_stride;
+        if (P->single_request && scr.d_tcarry_h && P->lane_stride) {
+            // one request: contiguous runs of tiles per CTA, carrying next hits
+            const uint32_t run = (e.ntiles + tgrid - 1) / tgrid;
+            if (((uint64_t)run << bt) <= (1ull << 31)) ta.run = run;
+        }
         prof_mark(c, SIEVE_K_TILE, st, true);
-        CK(launch_tiles(ta, std::min<uint32_t>(e.ntiles, tgrid_max), st));
+        CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));
         prof_mark(c, SIEVE_K_TILE, st, false);
         CK(cudaEventRecord(scr.ev_tile[b], st));
     }
@@ -563,7 +669,8 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
 sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long *counts, uint32_t ncounts,
                         cudaStream_t st, bool allow_graph)
 {
-    sieve_status s = scratch_ensure(c->scr, P->pool_entries, P->max_epoch_tiles);
+    const uint64_t tcarry = P->single_request ? (uint64_t)c->nsm * tile_blocks_per_sm(P->tune.tile_log2) * P->lane_stride : 0;
+    sieve_status s = scratch_ensure(c->scr, P->pool_entries, P->max_epoch_tiles, P->carry_entries, tcarry);
     if (s) return s;
     if (!P->d_tiles) {
         s = upload_plan(c, P, st);
@@ -752,6 +859,21 @@ sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_
         return s;
     }
     CK(cudaMemcpy(c->d_pat, c->pre.words.data(), c->pre.words.size() * 8, cudaMemcpyHostToDevice));
+    {
+        std::vector<uint32_t> gapw, rstate;
+        std::vector<uint16_t> winv;
+        build_big_wheel(gapw, rstate, winv);
+        s = alloc_dev((void **)&c->d_gapw, gapw.size() * 4);
+        if (!s) s = alloc_dev((void **)&c->d_rstate, rstate.size() * 4);
+        if (!s) s = alloc_dev((void **)&c->d_winv, winv.size() * 2);
+        if (s) {
+            sieve_destroy(c.release());
+            return s;
+        }
+        CK(cudaMemcpy(c->d_gapw, gapw.data(), gapw.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_rstate, rstate.data(), rstate.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_winv, winv.data(), winv.size() * 2, cudaMemcpyHostToDevice));
+    }
     CK(cudaMallocHost((void **)&c->h_acc, 64));
     CK(cudaMallocHost((void **)&c->h_err, 16));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -776,7 +898,8 @@ void sieve_destroy(sieve_ctx *c)
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     c->plans.clear();
-    for (void *p : {(void *)c->d_primes, (void *)c->d_barrett, (void *)c->d_pat, (void *)c->d_stage})
+    for (void *p : {(void *)c->d_primes, (void *)c->d_barrett, (void *)c->d_pat, (void *)c->d_stage,
+                    (void *)c->d_gapw, (void *)c->d_rstate, (void *)c->d_winv})
         if (p) cudaFree(p);
     scratch_free(c->scr);
     if (c->h_acc) cudaFreeHost(c->h_acc);

@@ -20,6 +20,7 @@ struct PresieveTable {
     uint32_t maxp[kMaxPresieveGroups];
 };
 void build_presieve(PresieveTable &t);
+void build_big_wheel(std::vector<uint32_t> &gapw, std::vector<uint32_t> &rstate, std::vector<uint16_t> &inv);
 
 struct ReqSpec {
     uint64_t j0, nbits, out_word;
@@ -38,10 +39,15 @@ struct Plan {
         uint32_t tile0, ntiles;  // tiles [tile0, tile0+ntiles)
         uint32_t g0, ng;         // scatter groups [g0, g0+ng)
         uint32_t c0, nc;         // scatter chunks (one CTA each) [c0, c0+nc)
+        uint32_t carry_base;     // first large prime index of the epoch's carried state
     };
     std::vector<Epoch> epochs;
     uint64_t pool_entries = 0;
     uint32_t max_epoch_tiles = 0;
+    uint64_t carry_entries = 0;  // carried-state slots the plan needs
+    bool single_request = false; // all tiles belong to one request (tile runs may carry)
+    bool big_wheel = false;      // large primes use the mod-15015 wheel (else mod 15)
+    uint32_t lane_stride = 0;    // one-prime-per-thread primes of the widest tile
     uint64_t bits = 0;
     double exp_large_hits = 0;
     // device copies of the descriptors
@@ -78,6 +84,12 @@ struct Scratch {
     uint32_t *d_small = nullptr;  // [0] tile work counter, [2+b] overflow count of pool b
     int *d_err = nullptr;         // device error bits
     unsigned long long *d_acc = nullptr;  // [0] popcount, [1] profiled hits
+    unsigned long long *d_carry = nullptr;  // next hit per large prime between groups
+    size_t carry_bytes = 0;
+    uint32_t *d_tcarry_h = nullptr;  // tile runs: next hit per (CTA, one-prime-per-thread prime)
+    size_t tcarry_h_bytes = 0;
+    uint8_t *d_tcarry_s = nullptr;
+    size_t tcarry_s_bytes = 0;
     uint64_t gen = 0;             // bumped when a buffer moves (captured graphs re-capture)
     uint64_t pool_entries = 0;    // capacity allowed per pool (entries)
     cudaStream_t s_tile = nullptr, s_scat = nullptr;  // high / low priority
@@ -86,7 +98,8 @@ struct Scratch {
 };
 sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap);
 void scratch_free(Scratch &s);
-sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles);
+sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoch_tiles,
+                            uint64_t carry_entries = 0, uint64_t tile_carry_entries = 0);
 }  // namespace gbs
 
 struct sieve_ctx {
@@ -99,6 +112,8 @@ struct sieve_ctx {
     std::vector<double> h_inv_prefix;  // sum of 1/p over the first k*kInvBlock primes
     gbs::PresieveTable pre;
     unsigned long long *d_pat = nullptr;
+    uint32_t *d_gapw = nullptr, *d_rstate = nullptr;  // mod-15015 wheel of the large primes
+    uint16_t *d_winv = nullptr;
     sieve_tuning tune[SIEVE_TUNE_CLASSES];
     size_t mem_budget = 0;
     gbs::Scratch scr;

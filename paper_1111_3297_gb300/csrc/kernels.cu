@@ -86,13 +86,21 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t ng = a.ps.ngroups;
 
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(a.work, 1u);
+    const uint32_t run_lo = a.run ? blockIdx.x * a.run : 0u;
+    const uint32_t run_hi = a.run ? min(a.ntiles, run_lo + a.run) : 0u;
+    for (uint32_t it = 0;; ++it) {
+        if (a.run) {
+            if (run_lo + it >= run_hi) break;
+            if (tid == 0) s_tile = run_lo + it;
+        } else if (tid == 0) {
+            s_tile = atomicAdd(a.work, 1u);
+        }
         __syncthreads();
         const uint32_t t = s_tile;
         if (t >= a.ntiles) break;
         const TileDesc d = a.tiles[t];
         const uint32_t len = d.len, nwords = len >> 5;
+        const bool carried = a.run && it > 0;  // the previous tile of this CTA ends where d starts
 
         // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
         // Two passes of up to 7 groups each (fewer live residues); the second
@@ -206,34 +214,58 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
             }
         }
         {
-            // one prime per thread, the next prime's loads issued ahead
+            // one prime per thread, the next prime's loads issued ahead; in a run of
+            // tiles the next hit carries over (relative to the next tile's start)
             const uint32_t end = d.med_hi;
-            uint32_t idx = max(max(a.med_lo, a.blk_hi), a.coop_hi) + tid;
-            uint32_t pn = 0;
+            const uint32_t lo = max(max(a.med_lo, a.blk_hi), a.coop_hi);
+            uint32_t *ch = a.carry_h + (size_t)blockIdx.x * a.carry_stride - lo;
+            uint8_t *cs = a.carry_s + (size_t)blockIdx.x * a.carry_stride - lo;
+            uint32_t idx = lo + tid;
+            uint32_t pn = 0, hn = 0, sn = 0;
             uint64_t mn = 0;
             if (idx < end) {
                 pn = a.primes[idx];
-                mn = a.barrett[idx];
+                if (carried) {
+                    hn = ch[idx];
+                    sn = cs[idx];
+                } else {
+                    mn = a.barrett[idx];
+                }
             }
             while (idx < end) {
                 const uint32_t p = pn;
                 const uint64_t m = mn;
+                const uint32_t hc = hn, sc = sn;
                 const uint32_t nidx = idx + T;
                 if (nidx < end) {
                     pn = a.primes[nidx];
-                    mn = a.barrett[nidx];
+                    if (carried) {
+                        hn = ch[nidx];
+                        sn = cs[nidx];
+                    } else {
+                        mn = a.barrett[nidx];
+                    }
+                }
+                uint32_t s = sc;
+                uint64_t hh = hc;
+                if (!carried) hh = first_hit(d.J, js15, p, m, s);
+                if (hh < len) {
+                    uint32_t h = (uint32_t)hh;
+                    for (;;) {
+                        atomicOr(&sm[h >> 5], 1u << (h & 31));
+                        h += wheel_gap(s) * p;  // medium primes < 2^28: no overflow
+                        s = (s + 1) & 7;
+                        if (h >= len) break;
+                    }
+                    hh = h;
+                }
+                if (a.run) {
+                    // next hit relative to the next tile; 0xFFFFFFFF (kept as is) when
+                    // it lies beyond the run, which spans at most 2^31 bits
+                    ch[idx] = hh >= (uint64_t)len + 0x7FFFFFFFull ? kStateInf : (uint32_t)(hh - len);
+                    cs[idx] = (uint8_t)s;
                 }
                 idx = nidx;
-                uint32_t s;
-                const uint64_t hh = first_hit(d.J, js15, p, m, s);
-                if (hh >= len) continue;
-                uint32_t h = (uint32_t)hh;
-                for (;;) {
-                    atomicOr(&sm[h >> 5], 1u << (h & 31));
-                    h += wheel_gap(s) * p;  // medium primes < 2^28: no overflow
-                    s = (s + 1) & 7;
-                    if (h >= len) break;
-                }
             }
         }
 
@@ -344,7 +376,7 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // (a group is <= kScatterMaxTiles tiles of one or more requests).  Prime-major: a
 // warp takes 32 primes (one per lane, prime and Barrett constant in registers),
 // walks the group's scatter units, computes each unit's first hit (Lemma lem:q,
-// the p^2 start of Sec. 1.4, the wheel of Sec. 3.2.1) and emits every hit of the
+// the p^2 start of Sec. 1.4, the mod-15015 or mod-15 wheel) and emits every hit of the
 // unit into its own staging buffer in shared memory, counting hits per tile as
 // it goes.  When a warp's buffer is full the CTA flushes: block scan of the
 // per-tile counts, one atomic reservation per (tile, flush) in the tile's
@@ -358,6 +390,9 @@ constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 512, kScE = kScNW * kScEW;
 constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
                            (size_t)kScatterMaxTiles * (8 + 8 + 8 + 4) /*tbase,tlim,gb,hist*/;
 
+// BIG: the mod-15015 wheel (fewest hits; its first hit reads two tables);
+// otherwise the mod-15 wheel (tables in registers: cheapest first hit)
+template <bool BIG>
 __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -390,28 +425,54 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
         __syncthreads();
 
         uint32_t lg = warp, su = g.su0;
-        bool need_load = true, need_hit = true;
-        uint32_t p = 0, h = kStateInf, s = 0;
-        uint64_t m = 0;
+        bool need_load = true, need_hit = true, pf = false;
+        uint32_t p = 0, h = kStateInf, s = 0, gw = 0, p_n = 0;
+        uint64_t m = 0, m_n = 0;
+        unsigned long long cs = 0, cs_n = 0;
         for (;;) {
             // ---- generate into the warp's staging buffer, counting per tile ----
             uint32_t wcnt = 0;
             bool full = false;
             while (lg < nlg) {
                 if (need_load) {
+                    // this lane group's prime, constant and carried state (prefetched
+                    // while the previous lane group was emitting), then the next one's
                     const uint32_t idx = lg * 32 + lane;
-                    p = idx < n ? a.primes[lo + idx] : 0u;
-                    m = idx < n ? a.barrett[lo + idx] : 0ull;
+                    if (pf) {
+                        p = p_n;
+                        m = m_n;
+                        cs = cs_n;
+                    } else {
+                        p = idx < n ? a.primes[lo + idx] : 0u;
+                        m = idx < n ? a.barrett[lo + idx] : 0ull;
+                        cs = (g.carry_in && idx < n) ? a.carry[lo + idx - a.carry_base] : 0ull;
+                    }
+                    const uint32_t ni = (lg + kScNW) * 32 + lane;
+                    pf = lg + kScNW < nlg;
+                    if (pf) {
+                        p_n = ni < n ? a.primes[lo + ni] : 0u;
+                        m_n = ni < n ? a.barrett[lo + ni] : 0ull;
+                        cs_n = (g.carry_in && ni < n) ? a.carry[lo + ni - a.carry_base] : 0ull;
+                    }
                     need_load = false;
                 }
                 const SUDesc u = a.sus[su];
                 if (need_hit) {
                     h = kStateInf;
                     s = 0;
-                    if (p != 0 && p <= u.plimit) {
-                        const uint64_t hh = first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
+                    const uint32_t idx = lg * 32 + lane;
+                    if (su == g.su0 && g.carry_in) {
+                        // continue from where this prime left the previous group
+                        if (idx < n) {
+                            h = (uint32_t)cs;
+                            s = (uint32_t)(cs >> 32);
+                        }
+                    } else if (p != 0 && p <= u.plimit) {
+                        const uint64_t hh = BIG ? first_hit_big(u.J, (uint32_t)(u.J % kBigW), p, m, a.wheel, s)
+                                                : first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
                         if (hh < kStateInf) h = (uint32_t)hh;
                     }
+                    gw = BIG ? __ldg(a.wheel.gapw + (s >> 3)) >> (4 * (s & 7)) : 0u;
                     need_hit = false;
                 }
                 const uint32_t ebase = u.tile_rel << bt;
@@ -427,14 +488,29 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                         const uint32_t v = ebase + h;
                         wb[wcnt + __popc(mask & lanemask_lt())] = v;
                         atomicAdd(&hist[v >> bt], 1u);
-                        const uint64_t nh = (uint64_t)h + (uint64_t)wheel_gap(s) * p;
-                        h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
-                        s = (s + 1) & 7;
+                        if (BIG) {
+                            const uint64_t nh = (uint64_t)h + (uint64_t)(gw & 15u) * p;
+                            h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
+                            gw >>= 4;
+                            if (++s == kBigCycle) s = 0;
+                            if ((s & 7) == 0) gw = __ldg(a.wheel.gapw + (s >> 3));
+                        } else {
+                            const uint64_t nh = (uint64_t)h + (uint64_t)wheel_gap(s) * p;
+                            h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
+                            s = (s + 1) & 7;
+                        }
                     }
                     wcnt += __popc(mask);
                 }
                 if (full) break;
                 need_hit = true;
+                if (su + 1 == su_end && g.carry_out) {
+                    // the next group starts where this unit ends: keep the next hit
+                    const uint32_t idx = lg * 32 + lane;
+                    if (idx < n)
+                        a.carry[lo + idx - a.carry_base] =
+                            ((unsigned long long)s << 32) | (h == kStateInf ? kStateInf : h - u.span);
+                }
                 if (++su == su_end) {
                     su = g.su0;
                     lg += kScNW;
@@ -493,9 +569,12 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
     }
 }
 
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, cudaStream_t st)
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, cudaStream_t st)
 {
-    k_scatter<<<nchunks, kScT, kScSmem, st>>>(a);
+    if (big_wheel)
+        k_scatter<true><<<nchunks, kScT, kScSmem, st>>>(a);
+    else
+        k_scatter<false><<<nchunks, kScT, kScSmem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -738,7 +817,8 @@ cudaError_t set_kernel_attributes()
     cudaError_t e = cudaFuncSetAttribute(k_tile<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
     return e;
 }
 

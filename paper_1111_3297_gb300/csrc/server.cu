@@ -132,7 +132,7 @@ bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
     const sieve_tuning t = c->batch_tune.tile_log2 ? c->batch_tune : c->tune[tune_class(vmax)];
     L.plan = build_plan(c, rs, t, L.scr.pool_entries);
     Plan *P = L.plan.get();
-    sieve_status s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles);
+    sieve_status s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles, P->carry_entries);
     if (!s) s = upload_plan(c, P, L.st);
     if (!s) s = enqueue_plan(c, L.scr, P, d_arena, L.d_counts, (uint32_t)batch.size(), L.st);
     if (!s && cudaMemcpyAsync(L.h_counts, L.d_counts, batch.size() * 8, cudaMemcpyDeviceToHost, L.st) != cudaSuccess)

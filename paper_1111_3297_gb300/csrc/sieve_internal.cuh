@@ -125,6 +125,50 @@ __device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32
 }
 
 // ---------------------------------------------------------------------------
+// Big wheel for large primes: W = 3*5*7*11*13 = 15015 (all five are always in the
+// first pre-sieve group), the same construction as the mod-15 wheel above but
+// keeping only the 5760 multiples p*c with c coprime to 15015.  Walking c -> c+2,
+// consecutive admissible residues are at most 11 steps apart, so the gaps are
+// packed 8 to a 32-bit word (4 bits each); the cycle (5760) is a multiple of 8.
+// Tables (built on the host, read through the L1):
+//   gapw[i]    gaps of cycle positions 8i..8i+7
+//   rstate[r]  for a residue r of c mod W: (steps to the first admissible residue
+//              from r) << 16 | (cycle position of that residue)
+//   inv[r]     r^{-1} mod W for r coprime to W
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBigW = 15015, kBigCycle = 5760, kBigWords = kBigCycle / 8;
+constexpr double kBigDensity = 5760.0 / 15015.0;  // struck multiples per multiple
+struct BigWheel {
+    const uint32_t *gapw;
+    const uint32_t *rstate;
+    const uint16_t *inv;
+};
+
+// As first_hit, with the mod-15015 wheel; jsw = Js mod 15015.
+__device__ __forceinline__ uint64_t first_hit_big(uint64_t Js, uint32_t jsw, uint32_t p, uint64_t m,
+                                                  const BigWheel &w, uint32_t &state)
+{
+    uint32_t r = mod_barrett(Js, p, m);
+    uint32_t half = p >> 1;
+    uint32_t q = (r <= half) ? (half - r) : (half + (p - r));
+    uint64_t jsq = ((uint64_t)p * p) >> 1;
+    uint64_t h;
+    uint32_t cw;
+    if (Js + q < jsq) {
+        h = jsq - Js;  // the number there is p*p, so c = p
+        cw = p % kBigW;
+    } else {
+        h = q;
+        // the number there is 2(Js+q)+1 = p*c, so c = (2(Js+q)+1) * p^{-1} (mod W)
+        const uint32_t mw = (2u * jsw + 2u * (q % kBigW) + 1u) % kBigW;
+        cw = (mw * (uint32_t)__ldg(w.inv + p % kBigW)) % kBigW;
+    }
+    const uint32_t e = __ldg(w.rstate + cw);
+    state = e & 0xFFFFu;
+    return h + (uint64_t)(e >> 16) * p;
+}
+
+// ---------------------------------------------------------------------------
 // Pre-sieve (Sec. 3.1): small primes are applied as periodic bit patterns.
 // Group g covers the primes whose product is P_g; bit rho (0 <= rho < P_g + 64)
 // of its pattern is 1 when some prime p of the group divides 2*rho+1 (rho = J
@@ -170,6 +214,9 @@ struct GroupDesc {      // scatter units sharing one flush domain (<= kScatterMa
     uint32_t su0, nsu;
     uint32_t tile0, ntiles;  // tiles [tile0, tile0+ntiles) of the launch's tile list
     uint32_t p_lo, p_hi;     // large primes: base indices [p_lo, p_hi)
+    uint32_t carry_in;       // 1: unit su0 continues the previous group's last unit (same
+                             // request, adjacent), so each prime's next hit is carried over
+    uint32_t carry_out;      // 1: the next group continues this group's last unit
 };
 
 struct ChunkDesc {      // one scatter CTA: large primes [p_lo, p_hi), through all groups of the epoch
@@ -201,6 +248,13 @@ struct TileArgs {
     uint32_t *out;
     unsigned long long *req_counts; // may be null
     uint32_t tile_log2;
+    // contiguous runs: CTA b takes tiles [b*run, (b+1)*run) in order and carries the
+    // one-prime-per-thread primes' next hits from a tile to the next (tiles of one
+    // request, each starting where the previous one ends); run = 0: work counter
+    uint32_t run;
+    uint32_t *carry_h;              // per CTA, per carried prime: next hit offset
+    uint8_t *carry_s;               // and wheel state
+    uint32_t carry_stride;          // carried primes per CTA
 };
 
 struct ScatterArgs {
@@ -211,6 +265,9 @@ struct ScatterArgs {
     const ChunkDesc *chunks;        // one per CTA
     uint32_t ngroups;               // groups of the epoch
     const TileDesc *tiles;          // bucket offset and capacity of every tile
+    unsigned long long *carry;      // per large prime (index - carry_base): next hit and wheel state
+    uint32_t carry_base;
+    BigWheel wheel;
     uint32_t *bkt;
     uint32_t *bkt_cnt;
     unsigned long long *ovf;
@@ -226,7 +283,7 @@ int tile_blocks_per_sm(uint32_t tile_log2);
 size_t tile_smem_bytes(uint32_t tile_log2);
 cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
 constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, cudaStream_t st);
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, cudaStream_t st);
 cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
 cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
                            uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out,
