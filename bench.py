@@ -419,17 +419,36 @@ def main():
                       "hits": h_large, "hbm_bytes": scatter_bytes,
                       "hbm_gbs": scatter_bytes / t_scatter / 1e9 if t_scatter else None},
     }
+    # DRAM traffic per launch from the committed ncu capture of the same kernel on a
+    # smaller slice of the same workload, scaled by the kernel's units per launch;
+    # null when kernels.cu changed since the capture
+    traffic = {"k_tile": None, "k_scatter": None}
+    try:
+        import hashlib
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ksha = hashlib.sha256(open(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc", "kernels.cu"),
+                                   "rb").read()).hexdigest()[:16]
+        key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n1024_mid2p60"}.get(args.workload)
+        if key and tj.get("kernels_cu_sha256_16") == ksha and key in tj:
+            tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
+            if n_tile:
+                traffic["k_tile"] = tt["dram_bytes"] / tt["units"] * (N / n_tile)
+            if n_scatter:
+                traffic["k_scatter"] = ts["dram_bytes"] / ts["units"] * (h_large / n_scatter)
+    except Exception:
+        pass
     if t_tile >= t_scatter:
         ach = marks / t_tile / 1e9
         roof = {"kernel": "k_tile", "bound": "smem_atomic", "achieved": ach, "peak": r_atom / 1e9,
-                "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": None,
+                "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": traffic["k_tile"],
                 "peak_source": "measured in this run (conflict-free shared atomicOr probe)",
                 "hbm_achieved_gbs": tile_bytes / t_tile / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": tile_bytes / t_tile / 1e9 / hbm_peak}
     else:
         ach = scatter_bytes / t_scatter / 1e9
         roof = {"kernel": "k_scatter", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+                "frac": ach / hbm_peak, "traffic": traffic["k_scatter"],
+                "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
     # step-level roofline: the slower of HBM bytes at peak and marks at the atomic peak
     step_s = ms_max * 1e-3 / steps
     b_alg = N / 8 + 16 * h_large + 4 * prof["prime_reads"] / steps
