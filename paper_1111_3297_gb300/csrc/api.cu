@@ -250,7 +250,6 @@ void scratch_free(Scratch &s)
             if (p) cudaFree(p);
     if (s.d_carry) cudaFree(s.d_carry);
     if (s.d_tcarry_h) cudaFree(s.d_tcarry_h);
-    if (s.d_tcarry_s) cudaFree(s.d_tcarry_s);
     for (void *p : {(void *)s.d_small, (void *)s.d_err, (void *)s.d_acc})
         if (p) cudaFree(p);
     if (s.s_tile) cudaStreamDestroy(s.s_tile);
@@ -266,7 +265,6 @@ sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoc
     if (pool_entries > s.pool_entries) return SIEVE_ENOMEM;
     if (tile_carry_entries) {
         sieve_status r = ensure((void **)&s.d_tcarry_h, &s.tcarry_h_bytes, (size_t)tile_carry_entries * 4, &s.gen);
-        if (!r) r = ensure((void **)&s.d_tcarry_s, &s.tcarry_s_bytes, (size_t)tile_carry_entries, &s.gen);
         if (r) return r;
     }
     if (carry_entries) {
@@ -360,10 +358,10 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     P->med_lo = prime_count_le(c, P->ps.max_prime);
     P->coop_hi = std::max(P->med_lo, prime_count_le(c, t.coop_max));
     {
-        // primes whose 60-multiple warp step still fits the tile slice of one warp
-        // are struck by the whole CTA
+        // primes whose 60-multiple warp step fits four times into the tile slice of
+        // one warp are struck by the whole CTA
         const uint32_t nw = (uint32_t)tile_threads(t.tile_log2) / 32;
-        P->blk_hi = std::max(P->med_lo, std::min(P->coop_hi, prime_count_le(c, (1ull << t.tile_log2) / (60 * nw))));
+        P->blk_hi = std::max(P->med_lo, std::min(P->coop_hi, prime_count_le(c, (1ull << t.tile_log2) / (240 * nw))));
     }
     const uint32_t large_lo = std::max(P->med_lo, prime_count_le(c, t.medium_max));
     const uint64_t pool_cap = pool_cap_in ? pool_cap_in : c->scr.pool_entries;
@@ -642,12 +640,12 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         const uint32_t tgrid = std::min<uint32_t>(e.ntiles, tgrid_max);
         ta.run = 0;
         ta.carry_h = scr.d_tcarry_h;
-        ta.carry_s = scr.d_tcarry_s;
         ta.carry_stride = P->lane_stride;
-        if (P->single_request && scr.d_tcarry_h && P->lane_stride) {
-            // one request: contiguous runs of tiles per CTA, carrying next hits
+        if (P->single_request && scr.d_tcarry_h && P->lane_stride && P->tune.medium_max <= (1u << 26)) {
+            // one request: contiguous runs of tiles per CTA, carrying next hits (offsets
+            // below 3 * medium_max <= 2^28 and run spans below 2^29 - 1 bits)
             const uint32_t run = (e.ntiles + tgrid - 1) / tgrid;
-            if (((uint64_t)run << bt) <= (1ull << 31)) ta.run = run;
+            if (((uint64_t)run << bt) < (1ull << 29) - 1) ta.run = run;
         }
         prof_mark(c, SIEVE_K_TILE, st, true);
         CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));

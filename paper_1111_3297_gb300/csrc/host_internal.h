@@ -88,8 +88,6 @@ struct Scratch {
     size_t carry_bytes = 0;
     uint32_t *d_tcarry_h = nullptr;  // tile runs: next hit per (CTA, one-prime-per-thread prime)
     size_t tcarry_h_bytes = 0;
-    uint8_t *d_tcarry_s = nullptr;
-    size_t tcarry_s_bytes = 0;
     uint64_t gen = 0;             // bumped when a buffer moves (captured graphs re-capture)
     uint64_t pool_entries = 0;    // capacity allowed per pool (entries)
     cudaStream_t s_tile = nullptr, s_scat = nullptr;  // high / low priority

@@ -177,7 +177,15 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                     if (hj >= E0) continue;
                     const uint32_t step = 60u * pj;
                     uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
-                    if (pos < S0) pos += (S0 - pos + step - 1) / step * step;
+                    if (pos < S0) {
+                        // skip to the first step at or after the slice start: the quotient
+                        // estimated in float, then corrected exactly
+                        const uint32_t d = S0 - pos;
+                        uint32_t k = __float2uint_rz(__uint2float_rn(d) * __frcp_rn(__uint2float_rn(step)));
+                        pos += k * step;
+                        while (pos < S0) pos += step;
+                        while (pos >= S0 + step) pos -= step;
+                    }
                     while (pos < E0) {
                         atomicOr(&sm[pos >> 5], 1u << (pos & 31));
                         pos += step;
@@ -218,36 +226,33 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
             // tiles the next hit carries over (relative to the next tile's start)
             const uint32_t end = d.med_hi;
             const uint32_t lo = max(max(a.med_lo, a.blk_hi), a.coop_hi);
+            // carried state: next hit offset (29 bits; all ones = beyond the run) and
+            // wheel state (3 bits)
             uint32_t *ch = a.carry_h + (size_t)blockIdx.x * a.carry_stride - lo;
-            uint8_t *cs = a.carry_s + (size_t)blockIdx.x * a.carry_stride - lo;
             uint32_t idx = lo + tid;
-            uint32_t pn = 0, hn = 0, sn = 0;
+            uint32_t pn = 0, cn = 0;
             uint64_t mn = 0;
             if (idx < end) {
                 pn = a.primes[idx];
-                if (carried) {
-                    hn = ch[idx];
-                    sn = cs[idx];
-                } else {
+                if (carried)
+                    cn = ch[idx];
+                else
                     mn = a.barrett[idx];
-                }
             }
             while (idx < end) {
                 const uint32_t p = pn;
                 const uint64_t m = mn;
-                const uint32_t hc = hn, sc = sn;
+                const uint32_t cc = cn;
                 const uint32_t nidx = idx + T;
                 if (nidx < end) {
                     pn = a.primes[nidx];
-                    if (carried) {
-                        hn = ch[nidx];
-                        sn = cs[nidx];
-                    } else {
+                    if (carried)
+                        cn = ch[nidx];
+                    else
                         mn = a.barrett[nidx];
-                    }
                 }
-                uint32_t s = sc;
-                uint64_t hh = hc;
+                uint32_t s = cc >> 29;
+                uint64_t hh = (cc & 0x1FFFFFFFu) == 0x1FFFFFFFu ? kStateInf : (cc & 0x1FFFFFFFu);
                 if (!carried) hh = first_hit(d.J, js15, p, m, s);
                 if (hh < len) {
                     uint32_t h = (uint32_t)hh;
@@ -260,10 +265,10 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                     hh = h;
                 }
                 if (a.run) {
-                    // next hit relative to the next tile; 0xFFFFFFFF (kept as is) when
-                    // it lies beyond the run, which spans at most 2^31 bits
-                    ch[idx] = hh >= (uint64_t)len + 0x7FFFFFFFull ? kStateInf : (uint32_t)(hh - len);
-                    cs[idx] = (uint8_t)s;
+                    // next hit relative to the next tile; all ones (kept as is) when it
+                    // lies beyond the run, which spans less than 2^29 - 1 bits
+                    const uint32_t off = hh >= (uint64_t)len + 0x1FFFFFFFull ? 0x1FFFFFFFu : (uint32_t)(hh - len);
+                    ch[idx] = (s << 29) | off;
                 }
                 idx = nidx;
             }

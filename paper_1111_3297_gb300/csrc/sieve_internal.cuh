@@ -252,8 +252,7 @@ struct TileArgs {
     // one-prime-per-thread primes' next hits from a tile to the next (tiles of one
     // request, each starting where the previous one ends); run = 0: work counter
     uint32_t run;
-    uint32_t *carry_h;              // per CTA, per carried prime: next hit offset
-    uint8_t *carry_s;               // and wheel state
+    uint32_t *carry_h;              // per CTA, per carried prime: wheel state << 29 | next hit offset
     uint32_t carry_stride;          // carried primes per CTA
 };
 
