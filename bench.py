@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="JSON tuning to use as is (no autotune), e.g. for profiling")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--segments", type=int, default=0, help="override n (small profiling cases)")
@@ -327,7 +328,11 @@ def main():
     out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
 
     tuned = None
-    if not args.no_autotune:
+    if args.tuning:
+        tuned = json.loads(args.tuning)
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **tuned)
+    elif not args.no_autotune:
         tuned = S.sieve_autotune(ctx, l, f, n)
     r_atom = S.sieve_probe_smem_atomics(local)
 
@@ -428,7 +433,7 @@ def main():
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         ksha = hashlib.sha256(open(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc", "kernels.cu"),
                                    "rb").read()).hexdigest()[:16]
-        key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n1024_mid2p60"}.get(args.workload)
+        key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload)
         if key and tj.get("kernels_cu_sha256_16") == ksha and key in tj:
             tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
             if n_tile:
