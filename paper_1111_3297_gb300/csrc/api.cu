@@ -217,7 +217,8 @@ namespace gbs {
 
 sieve_status scratch_init(Scratch &s, uint64_t pool_entries, uint32_t ovf_cap)
 {
-    s.pool_entries = pool_entries;
+    // bucket slots are addressed with 32-bit offsets inside a pool
+    s.pool_entries = std::min<uint64_t>(pool_entries, (1ull << 32) - (1ull << 22));
     s.ovf_cap = ovf_cap;
     sieve_status r = alloc_dev((void **)&s.d_small, 64);
     if (!r) r = alloc_dev((void **)&s.d_err, 16);
@@ -494,16 +495,35 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
     make_chunks(c, P.get());
     P->single_request = reqs.size() == 1;
+    // one interval whose groups each form one unit continuing the previous group:
+    // the scatter keeps one state word per large prime for the whole interval
+    // (48-bit next-hit offsets: the interval stays below 2^47 bits)
+    P->run_scatter = P->single_request && !P->groups.empty() && P->bits < (1ull << 47);
+    for (size_t g = 0; P->run_scatter && g < P->groups.size(); ++g) {
+        const GroupDesc &G = P->groups[g];
+        P->run_scatter = G.nsu == 1 && G.p_lo == P->groups[0].p_lo && G.p_hi == P->groups[0].p_hi &&
+                         (g == 0 || P->sus[P->groups[g - 1].su0].J + P->sus[P->groups[g - 1].su0].span ==
+                                        P->sus[G.su0].J);
+    }
+    if (P->run_scatter) {
+        P->state_base = P->groups[0].p_lo;
+        // + one lane group of padding: lanes past a chunk's end load, never store
+        P->carry_entries = (uint64_t)(P->groups[0].p_hi - P->groups[0].p_lo) + 32;
+    }
     {
         const uint32_t lane_lo = std::max(std::max(P->med_lo, P->blk_hi), P->coop_hi);
         for (const ReqInfo &ri : info) P->lane_stride = std::max(P->lane_stride, ri.med_hi > lane_lo ? ri.med_hi - lane_lo : 0u);
     }
-    // carry each prime's next hit from a group to the next when the next group
-    // starts exactly where this one's last unit ends (same request) and both
-    // cover the same primes (then every CTA walks both with the same primes)
+    // otherwise carry each prime's next hit from a group to the next when the next
+    // group starts exactly where this one's last unit ends (same request) and both
+    // cover the same primes (then every CTA walks both with the same primes); the
+    // carried offset is 32-bit, so only inside epochs of at most 2^32 bits
     for (Plan::Epoch &e : P->epochs) {
         e.carry_base = ~0u;
         for (uint32_t g = 0; g < e.ng; ++g) e.carry_base = std::min(e.carry_base, P->groups[e.g0 + g].p_lo);
+        uint64_t ebits = 0;
+        for (uint32_t k = 0; k < e.ntiles; ++k) ebits += P->tiles[e.tile0 + k].len;
+        if (P->run_scatter || ebits > (1ull << 32)) continue;
         for (uint32_t g = 0; g + 1 < e.ng; ++g) {
             GroupDesc &A = P->groups[e.g0 + g], &B = P->groups[e.g0 + g + 1];
             const SUDesc &ua = P->sus[A.su0 + A.nsu - 1], &ub = P->sus[B.su0];
@@ -583,6 +603,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
     CK(cudaStreamWaitEvent(ss, scr.ev_fork, 0));
     if (counts && ncounts) CK(cudaMemsetAsync(counts, 0, (size_t)ncounts * 8, st));
+    bool run_first = true;
     for (size_t ei = 0; ei < P->epochs.size(); ++ei) {
         const Plan::Epoch &e = P->epochs[ei];
         const int b = (int)(ei & 1);
@@ -600,6 +621,10 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.tiles = P->d_tiles + e.tile0;
             sa.carry = scr.d_carry;
             sa.carry_base = e.carry_base;
+            sa.state = scr.d_carry;
+            sa.state_base = P->state_base;
+            sa.run_first = run_first ? 1u : 0u;
+            run_first = false;
             sa.wheel.gapw = c->d_gapw;
             sa.wheel.rstate = c->d_rstate;
             sa.wheel.inv = c->d_winv;
@@ -611,7 +636,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.err = scr.d_err;
             sa.tile_log2 = bt;
             prof_mark(c, SIEVE_K_SCATTER, ss, true);
-            CK(launch_scatter(sa, e.nc, P->big_wheel, ss));
+            CK(launch_scatter(sa, e.nc, P->big_wheel, P->run_scatter, ss));
             prof_mark(c, SIEVE_K_SCATTER, ss, false);
             if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt[b], e.ntiles, scr.d_acc + 1, ss));
             CK(cudaEventRecord(scr.ev_scat[b], ss));
@@ -743,8 +768,10 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
     if (limit <= 131071) {
         const uint64_t np = std::upper_bound(boot.begin(), boot.end(), (uint32_t)limit) - boot.begin();
         c->nprimes = np;
-        s = alloc_dev((void **)&c->d_primes, std::max<uint64_t>(np, 1) * 4);
+        // + kPrimePad zero entries: the scatter's lane groups read up to 31 past a chunk
+        s = alloc_dev((void **)&c->d_primes, (np + kPrimePad) * 4);
         if (s) return s;
+        CK(cudaMemset(c->d_primes, 0, (np + kPrimePad) * 4));
         if (np) CK(cudaMemcpy(c->d_primes, d_boot, np * 4, cudaMemcpyDeviceToDevice));
     } else {
         // sieve indices 0..jmax (numbers 1..limit) with the bootstrap primes
@@ -798,9 +825,11 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         CK(launch_tiles(ta, std::min<uint32_t>(ta.ntiles, (uint32_t)(c->nsm * tile_blocks_per_sm(bt))), st));
         // compact the zero bits 1..jmax into the ascending prime list
         const double lx = std::log((double)limit);
-        const uint64_t cap = (uint64_t)(1.25506 * (double)limit / lx) + 64;  // Rosser-Schoenfeld bound on pi(x)
+        // Rosser-Schoenfeld bound on pi(x), + kPrimePad zero entries past the last prime
+        const uint64_t cap = (uint64_t)(1.25506 * (double)limit / lx) + kPrimePad;
         s = alloc_dev((void **)&c->d_primes, cap * 4);
         if (s) return s;
+        CK(cudaMemsetAsync(c->d_primes, 0, cap * 4, st));
         const uint64_t nwords = nbits / 32;
         const uint32_t nblocks = (uint32_t)((nwords + 4095) / 4096);
         uint32_t *d_bc = nullptr, *d_bo = nullptr;
@@ -813,7 +842,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         uint32_t np = 0;
         CK(cudaMemcpyAsync(&np, d_cnt, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (np > cap) return SIEVE_ECUDA;
+        if (np + kPrimePad > cap) return SIEVE_ECUDA;
         c->nprimes = np;
     }
     s = alloc_dev((void **)&c->d_barrett, std::max<uint64_t>(c->nprimes, 1) * 8);

@@ -27,6 +27,8 @@ struct ReqSpec {
     uint32_t idx;
 };
 
+constexpr uint64_t kPrimePad = 64;  // zero entries allocated past the last base prime
+
 struct Plan {
     sieve_tuning tune;
     PresieveInfo ps;
@@ -46,6 +48,8 @@ struct Plan {
     uint32_t max_epoch_tiles = 0;
     uint64_t carry_entries = 0;  // carried-state slots the plan needs
     bool single_request = false; // all tiles belong to one request (tile runs may carry)
+    bool run_scatter = false;    // single-request scatter: one state word per large prime
+    uint32_t state_base = 0;     //   for the whole interval, primes from index state_base
     bool big_wheel = false;      // large primes use the mod-15015 wheel (else mod 15)
     uint32_t lane_stride = 0;    // one-prime-per-thread primes of the widest tile
     uint64_t bits = 0;

@@ -393,7 +393,87 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // ---------------------------------------------------------------------------
 constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 512, kScE = kScNW * kScEW;
 constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
-                           (size_t)kScatterMaxTiles * (8 + 8 + 8 + 4) /*tbase,tlim,gb,hist*/;
+                           (size_t)kScatterMaxTiles * 4 * 4 /*tbase, tlim, gb, hist*/;
+
+// Shared-memory layout of both scatter kernels.  Bucket slots are 32-bit entry
+// offsets into the epoch's pool (its size is capped below 2^32 entries).
+struct ScShared {
+    uint32_t *tbase, *tlim, *gb, *hist, *buf, *srt;
+    __device__ explicit ScShared(unsigned char *raw)
+    {
+        tbase = reinterpret_cast<uint32_t *>(raw);
+        tlim = tbase + kScatterMaxTiles;
+        gb = tlim + kScatterMaxTiles;
+        hist = gb + kScatterMaxTiles;
+        buf = hist + kScatterMaxTiles;
+        srt = buf + kScE;
+    }
+};
+
+// bucket ranges of the group's tiles, per-tile counters zeroed
+__device__ __forceinline__ void scatter_group_setup(const ScatterArgs &a, const GroupDesc &g, ScShared &sh)
+{
+    for (uint32_t k = threadIdx.x; k < g.ntiles; k += kScT) {
+        const TileDesc &td = a.tiles[g.tile0 + k];
+        sh.tbase[k] = (uint32_t)td.bkt_off;
+        sh.tlim[k] = (uint32_t)td.bkt_off + td.bkt_cap;
+        sh.hist[k] = 0;
+    }
+    __syncthreads();
+}
+
+// One flush of the CTA's staging buffers (every warp calls it after a barrier):
+// block scan of the per-tile counts, one atomic reservation per non-empty tile
+// (issued before the sort, consumed after it), a counting sort of each warp's
+// entries by tile, and a store pass in which consecutive lanes write consecutive
+// slots of one bucket.  Slots beyond a bucket's capacity go to the backstop list.
+__device__ __forceinline__ void scatter_flush(const ScatterArgs &a, const GroupDesc &g, ScShared &sh,
+                                              const uint32_t *wb, uint32_t wcnt, uint32_t *s_warp)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    const uint32_t bt = a.tile_log2, Bm = (1u << bt) - 1;
+    const uint32_t k0 = 2 * tid;
+    const uint32_t c0 = k0 < g.ntiles ? sh.hist[k0] : 0u, c1 = k0 + 1 < g.ntiles ? sh.hist[k0 + 1] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan<kScT>(c0 + c1, s_warp, &total);
+    // the counters become sort cursors
+    uint32_t r0 = 0, r1 = 0;
+    if (k0 < g.ntiles) {
+        sh.hist[k0] = ex;
+        if (c0) r0 = atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
+    }
+    if (k0 + 1 < g.ntiles) {
+        sh.hist[k0 + 1] = ex + c0;
+        if (c1) r1 = atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
+    }
+    __syncthreads();
+    for (uint32_t i = lane; i < wcnt; i += 32) {
+        const uint32_t v = wb[i];
+        sh.srt[atomicAdd(&sh.hist[v >> bt], 1u)] = v;
+    }
+    // sorted position i of tile k goes to slot gb[k] + i (32-bit, wrapping: the
+    // sum lands in [tbase, tbase + reserved))
+    if (c0) sh.gb[k0] = sh.tbase[k0] + r0 - ex;
+    if (c1) sh.gb[k0 + 1] = sh.tbase[k0 + 1] + r1 - (ex + c0);
+    __syncthreads();
+    for (uint32_t i = tid; i < total; i += kScT) {
+        const uint32_t v = sh.srt[i];
+        const uint32_t k = v >> bt;
+        const uint32_t dst = sh.gb[k] + i;
+        const uint32_t off = v & Bm;
+        if (dst < sh.tlim[k]) {
+            a.bkt[dst] = off;
+        } else {
+            const uint32_t o = atomicAdd(a.ovf_cnt, 1u);
+            if (o < a.ovf_cap)
+                a.ovf[o] = ((unsigned long long)(g.tile0 + k) << 32) | off;
+            else
+                atomicOr(a.err, kErrOverflow);
+        }
+    }
+    // cursors are no longer read: zero the counts for the next round
+    for (uint32_t k = tid; k < g.ntiles; k += kScT) sh.hist[k] = 0;
+}
 
 // BIG: the mod-15015 wheel (fewest hits; its first hit reads two tables);
 // otherwise the mod-15 wheel (tables in registers: cheapest first hit)
@@ -401,19 +481,14 @@ template <bool BIG>
 __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    unsigned long long *tbase = reinterpret_cast<unsigned long long *>(smraw);
-    unsigned long long *tlim = tbase + kScatterMaxTiles;
-    unsigned long long *gb = tlim + kScatterMaxTiles;
-    uint32_t *buf = reinterpret_cast<uint32_t *>(gb + kScatterMaxTiles);
-    uint32_t *srt = buf + kScE;
-    uint32_t *hist = srt + kScE;
+    ScShared sh(smraw);
     __shared__ uint32_t s_warp[33];
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const ChunkDesc ch = a.chunks[blockIdx.x];
     const uint32_t lo = ch.p_lo;
-    const uint32_t bt = a.tile_log2, Bm = (1u << bt) - 1;
-    uint32_t *wb = buf + warp * kScEW;
+    const uint32_t bt = a.tile_log2;
+    uint32_t *wb = sh.buf + warp * kScEW;
 
     for (uint32_t gi = 0; gi < a.ngroups; ++gi) {
         const GroupDesc g = a.groups[gi];
@@ -421,13 +496,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
         const uint32_t n = min(ch.p_hi, g.p_hi) - lo;
         const uint32_t nlg = (n + 31) / 32;
         const uint32_t su_end = g.su0 + g.nsu;
-        for (uint32_t k = tid; k < g.ntiles; k += kScT) {
-            const TileDesc &td = a.tiles[g.tile0 + k];
-            tbase[k] = td.bkt_off;
-            tlim[k] = td.bkt_off + td.bkt_cap;
-            hist[k] = 0;
-        }
-        __syncthreads();
+        scatter_group_setup(a, g, sh);
 
         uint32_t lg = warp, su = g.su0;
         bool need_load = true, need_hit = true, pf = false;
@@ -492,7 +561,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                     if (act) {
                         const uint32_t v = ebase + h;
                         wb[wcnt + __popc(mask & lanemask_lt())] = v;
-                        atomicAdd(&hist[v >> bt], 1u);
+                        atomicAdd(&sh.hist[v >> bt], 1u);
                         if (BIG) {
                             const uint64_t nh = (uint64_t)h + (uint64_t)(gw & 15u) * p;
                             h = nh >= kStateInf ? kStateInf : (uint32_t)nh;
@@ -511,6 +580,8 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                 need_hit = true;
                 if (su + 1 == su_end && g.carry_out) {
                     // the next group starts where this unit ends: keep the next hit
+                    // (the host carries only inside epochs of at most 2^32 bits, so a
+                    // saturated next hit lies beyond the epoch)
                     const uint32_t idx = lg * 32 + lane;
                     if (idx < n)
                         a.carry[lo + idx - a.carry_base] =
@@ -524,62 +595,141 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
             }
             const bool more = lg < nlg;
             __syncthreads();
-
-            // ---- flush: scan of the per-tile counts (two counters per thread) ----
-            const uint32_t k0 = 2 * tid;
-            const uint32_t c0 = k0 < g.ntiles ? hist[k0] : 0u, c1 = k0 + 1 < g.ntiles ? hist[k0 + 1] : 0u;
-            uint32_t total;
-            const uint32_t ex = block_excl_scan<kScT>(c0 + c1, s_warp, &total);
-            // the counters become sort cursors; one bucket reservation per non-empty
-            // tile is issued now and its result consumed after the sort
-            uint32_t r0 = 0, r1 = 0;
-            if (k0 < g.ntiles) {
-                hist[k0] = ex;
-                if (c0) r0 = atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
-            }
-            if (k0 + 1 < g.ntiles) {
-                hist[k0 + 1] = ex + c0;
-                if (c1) r1 = atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
-            }
-            __syncthreads();
-            // ---- each warp sorts its own entries by tile ----
-            for (uint32_t i = lane; i < wcnt; i += 32) {
-                const uint32_t v = wb[i];
-                srt[atomicAdd(&hist[v >> bt], 1u)] = v;
-            }
-            // sorted position i of tile k goes to bucket slot gb[k] + i
-            if (c0) gb[k0] = tbase[k0] + r0 - ex;
-            if (c1) gb[k0 + 1] = tbase[k0 + 1] + r1 - (ex + c0);
-            __syncthreads();
-            // ---- store: consecutive lanes -> consecutive slots of one bucket ----
-            for (uint32_t i = tid; i < total; i += kScT) {
-                const uint32_t v = srt[i];
-                const uint32_t k = v >> bt;
-                const unsigned long long dst = gb[k] + i;
-                const uint32_t off = v & Bm;
-                if (dst < tlim[k]) {
-                    a.bkt[dst] = off;
-                } else {
-                    const uint32_t o = atomicAdd(a.ovf_cnt, 1u);
-                    if (o < a.ovf_cap)
-                        a.ovf[o] = ((unsigned long long)(g.tile0 + k) << 32) | off;
-                    else
-                        atomicOr(a.err, kErrOverflow);
-                }
-            }
-            // cursors are no longer read: zero the counts for the next round
-            for (uint32_t k = tid; k < g.ntiles; k += kScT) hist[k] = 0;
+            scatter_flush(a, g, sh, wb, wcnt, s_warp);
             if (!__syncthreads_or(more)) break;
         }
     }
 }
 
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// Scatter of a single request (one contiguous interval): every group is one
+// scatter unit and starts where the previous one ends, across epochs too, so
+// each large prime keeps one 64-bit state word for the whole interval -- its
+// next hit relative to the start of the next group to be scattered (48 bits;
+// all ones = none left) and its wheel position (16 bits).  First hits (Lemma
+// lem:q, the p^2 start of Sec. 1.4, the wheel) are computed once, by the first
+// group of the interval; every later visit reads the word, emits the prime's
+// hits in the group and writes the word back.  Lanes past the chunk's end load
+// padding and stay idle.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kRunInf = (1ull << 48) - 1;
+
+template <bool BIG>
+__global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
 {
-    if (big_wheel)
-        k_scatter<true><<<nchunks, kScT, kScSmem, st>>>(a);
-    else
-        k_scatter<false><<<nchunks, kScT, kScSmem, st>>>(a);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ScShared sh(smraw);
+    __shared__ uint32_t s_warp[33];
+
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const ChunkDesc ch = a.chunks[blockIdx.x];
+    const uint32_t n = ch.p_hi - ch.p_lo;  // every group covers the chunk's primes
+    const uint32_t nlg = (n + 31) / 32;
+    const uint32_t bt = a.tile_log2;
+    const uint32_t *pr = a.primes + ch.p_lo;
+    const uint64_t *pm = a.barrett + ch.p_lo;
+    unsigned long long *stw = a.state + (ch.p_lo - a.state_base);
+    uint32_t *wb = sh.buf + warp * kScEW;
+
+    for (uint32_t gi = 0; gi < a.ngroups; ++gi) {
+        const GroupDesc g = a.groups[gi];
+        const SUDesc u = a.sus[g.su0];
+        const bool first = a.run_first && gi == 0;
+        const uint32_t span = u.span, ebase = u.tile_rel << bt;
+        const uint32_t jsx = first ? (BIG ? (uint32_t)(u.J % kBigW) : (uint32_t)(u.J % 15u)) : 0u;
+        scatter_group_setup(a, g, sh);
+
+        // the current lane group's state and the next one's words, loaded ahead
+        uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0;
+        uint64_t h = kRunInf;
+        bool need = true;
+        uint32_t p_n = 0;
+        unsigned long long w_n = 0;
+        if (lg < nlg) {
+            p_n = pr[lg * 32 + lane];
+            if (!first) w_n = stw[lg * 32 + lane];
+        }
+        for (;;) {
+            uint32_t wcnt = 0;
+            bool full = false;
+            while (lg < nlg) {
+                if (need) {
+                    idx = lg * 32 + lane;
+                    p = p_n;
+                    const unsigned long long w = w_n;
+                    const uint32_t nl = lg + kScNW;
+                    if (nl < nlg) {
+                        p_n = pr[nl * 32 + lane];
+                        if (!first) w_n = stw[nl * 32 + lane];
+                    }
+                    h = kRunInf;
+                    s = 0;
+                    if (idx < n) {
+                        if (first) {
+                            if (p <= u.plimit) {
+                                const uint64_t hh = BIG ? first_hit_big(u.J, jsx, p, pm[idx], a.wheel, s)
+                                                        : first_hit(u.J, jsx, p, pm[idx], s);
+                                h = hh < kRunInf ? hh : kRunInf;
+                            }
+                        } else {
+                            h = w & kRunInf;
+                            s = (uint32_t)(w >> 48);
+                        }
+                    }
+                    gw = (BIG && h < span) ? __ldg(a.wheel.gapw + (s >> 3)) >> (4 * (s & 7)) : 0u;
+                    need = false;
+                }
+                for (;;) {
+                    const bool act = h < span;
+                    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+                    if (!mask) break;
+                    if (wcnt + 32 > (uint32_t)kScEW) {
+                        full = true;
+                        break;
+                    }
+                    if (act) {
+                        const uint32_t v = ebase + (uint32_t)h;
+                        wb[wcnt + __popc(mask & lanemask_lt())] = v;
+                        atomicAdd(&sh.hist[v >> bt], 1u);
+                        if (BIG) {
+                            h += (uint64_t)(gw & 15u) * p;
+                            gw >>= 4;
+                            if (++s == kBigCycle) s = 0;
+                            if ((s & 7) == 0) gw = __ldg(a.wheel.gapw + (s >> 3));
+                        } else {
+                            h += (uint64_t)wheel_gap(s) * p;
+                            s = (s + 1) & 7;
+                        }
+                    }
+                    wcnt += __popc(mask);
+                }
+                if (full) break;
+                // next hit relative to the next group (h < span + 11 p < 2^48 unless none)
+                if (idx < n) stw[idx] = ((unsigned long long)s << 48) | (h == kRunInf ? kRunInf : h - span);
+                lg += kScNW;
+                need = true;
+            }
+            const bool more = lg < nlg;
+            __syncthreads();
+            scatter_flush(a, g, sh, wb, wcnt, s_warp);
+            if (!__syncthreads_or(more)) break;
+        }
+    }
+}
+
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, bool run, cudaStream_t st)
+{
+    if (run) {
+        if (big_wheel)
+            k_scatter_run<true><<<nchunks, kScT, kScSmem, st>>>(a);
+        else
+            k_scatter_run<false><<<nchunks, kScT, kScSmem, st>>>(a);
+    } else {
+        if (big_wheel)
+            k_scatter<true><<<nchunks, kScT, kScSmem, st>>>(a);
+        else
+            k_scatter<false><<<nchunks, kScT, kScSmem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -824,6 +974,8 @@ cudaError_t set_kernel_attributes()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter_run<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
     return e;
 }
 

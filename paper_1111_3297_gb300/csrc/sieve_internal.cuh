@@ -266,6 +266,11 @@ struct ScatterArgs {
     const TileDesc *tiles;          // bucket offset and capacity of every tile
     unsigned long long *carry;      // per large prime (index - carry_base): next hit and wheel state
     uint32_t carry_base;
+    // single-request scatter: per large prime (index - state_base) a state word that
+    // lives through all epochs; run_first = 1 when group 0 is the interval's first
+    unsigned long long *state;
+    uint32_t state_base;
+    uint32_t run_first;
     BigWheel wheel;
     uint32_t *bkt;
     uint32_t *bkt_cnt;
@@ -282,7 +287,8 @@ int tile_blocks_per_sm(uint32_t tile_log2);
 size_t tile_smem_bytes(uint32_t tile_log2);
 cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
 constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
-cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, cudaStream_t st);
+// run: the single-request kernel (every group one unit continuing the previous one)
+cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, bool run, cudaStream_t st);
 cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
 cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
                            uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out,
