@@ -838,7 +838,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         if (s) return s;
         guard.p.push_back(d_bc);
         guard.p.push_back(d_bo);
-        CK(launch_compact(d_tab, nbits, jmax, d_bc, d_bo, c->d_primes, d_cnt, st));
+        CK(launch_compact(d_tab, nbits, jmax, d_bc, d_bo, c->d_primes, cap, d_cnt, st));
         uint32_t np = 0;
         CK(cudaMemcpyAsync(&np, d_cnt, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

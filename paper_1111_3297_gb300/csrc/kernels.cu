@@ -256,12 +256,17 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                 if (!carried) hh = first_hit(d.J, js15, p, m, s);
                 if (hh < len) {
                     uint32_t h = (uint32_t)hh;
+                    // gaps of the mod-15 wheel from state s on, 2 bits each: the packed
+                    // cycle doubled to 32 bits, so a rotate by 2 is one wheel step
+                    uint32_t gq = __funnelshift_r(kGapPacked * 0x10001u, kGapPacked * 0x10001u, 2 * s), k = 0;
                     for (;;) {
                         atomicOr(&sm[h >> 5], 1u << (h & 31));
-                        h += wheel_gap(s) * p;  // medium primes < 2^28: no overflow
-                        s = (s + 1) & 7;
+                        h += (gq & 3u) * p;  // medium primes < 2^28: no overflow
+                        gq = __funnelshift_r(gq, gq, 2);
+                        ++k;
                         if (h >= len) break;
                     }
+                    s = (s + k) & 7;
                     hh = h;
                 }
                 if (a.run) {
@@ -280,6 +285,7 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
             const uint32_t *e = a.bkt + d.bkt_off;
             const uint32_t n4 = cnt >> 2;
             const uint4 *e4 = reinterpret_cast<const uint4 *>(e);
+#pragma unroll 4  // several 16-byte loads in flight per thread
             for (uint32_t i = tid; i < n4; i += T) {
                 const uint4 v = __ldcs(e4 + i);
                 atomicOr(&sm[v.x >> 5], 1u << (v.x & 31));
@@ -392,6 +398,8 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // spills to a global backstop list instead.
 // ---------------------------------------------------------------------------
 constexpr int kScT = 512, kScNW = kScT / 32, kScEW = 512, kScE = kScNW * kScEW;
+constexpr uint32_t kCPT = kScatterMaxTiles / kScT;  // tile counters per thread in a flush
+static_assert(kScatterMaxTiles % kScT == 0, "flush scan covers every tile");
 constexpr size_t kScSmem = (size_t)kScE * 4 * 2 /*buf, srt*/ +
                            (size_t)kScatterMaxTiles * 4 * 4 /*tbase, tlim, gb, hist*/;
 
@@ -432,19 +440,27 @@ __device__ __forceinline__ void scatter_flush(const ScatterArgs &a, const GroupD
 {
     const uint32_t tid = threadIdx.x, lane = tid & 31;
     const uint32_t bt = a.tile_log2, Bm = (1u << bt) - 1;
-    const uint32_t k0 = 2 * tid;
-    const uint32_t c0 = k0 < g.ntiles ? sh.hist[k0] : 0u, c1 = k0 + 1 < g.ntiles ? sh.hist[k0 + 1] : 0u;
-    uint32_t total;
-    const uint32_t ex = block_excl_scan<kScT>(c0 + c1, s_warp, &total);
-    // the counters become sort cursors
-    uint32_t r0 = 0, r1 = 0;
-    if (k0 < g.ntiles) {
-        sh.hist[k0] = ex;
-        if (c0) r0 = atomicAdd(&a.bkt_cnt[g.tile0 + k0], c0);
+    // thread tid scans the counters of tiles [kCPT*tid, kCPT*tid + kCPT)
+    const uint32_t k0 = kCPT * tid;
+    uint32_t c[kCPT], r[kCPT], sum = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < kCPT; ++j) {
+        c[j] = k0 + j < g.ntiles ? sh.hist[k0 + j] : 0u;
+        sum += c[j];
     }
-    if (k0 + 1 < g.ntiles) {
-        sh.hist[k0 + 1] = ex + c0;
-        if (c1) r1 = atomicAdd(&a.bkt_cnt[g.tile0 + k0 + 1], c1);
+    uint32_t total;
+    const uint32_t ex = block_excl_scan<kScT>(sum, s_warp, &total);
+    // the counters become sort cursors; one reservation per non-empty tile is
+    // issued now and its result consumed after the sort
+    uint32_t run = ex;
+#pragma unroll
+    for (uint32_t j = 0; j < kCPT; ++j) {
+        r[j] = 0;
+        if (k0 + j < g.ntiles) {
+            sh.hist[k0 + j] = run;
+            if (c[j]) r[j] = atomicAdd(&a.bkt_cnt[g.tile0 + k0 + j], c[j]);
+        }
+        run += c[j];
     }
     __syncthreads();
     for (uint32_t i = lane; i < wcnt; i += 32) {
@@ -453,8 +469,12 @@ __device__ __forceinline__ void scatter_flush(const ScatterArgs &a, const GroupD
     }
     // sorted position i of tile k goes to slot gb[k] + i (32-bit, wrapping: the
     // sum lands in [tbase, tbase + reserved))
-    if (c0) sh.gb[k0] = sh.tbase[k0] + r0 - ex;
-    if (c1) sh.gb[k0 + 1] = sh.tbase[k0 + 1] + r1 - (ex + c0);
+    run = ex;
+#pragma unroll
+    for (uint32_t j = 0; j < kCPT; ++j) {
+        if (c[j]) sh.gb[k0 + j] = sh.tbase[k0 + j] + r[j] - run;
+        run += c[j];
+    }
     __syncthreads();
     for (uint32_t i = tid; i < total; i += kScT) {
         const uint32_t v = sh.srt[i];
@@ -640,7 +660,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         scatter_group_setup(a, g, sh);
 
         // the current lane group's state and the next one's words, loaded ahead
-        uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0;
+        uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0, gwi = 0;
         uint64_t h = kRunInf;
         bool need = true;
         uint32_t p_n = 0;
@@ -676,7 +696,8 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                             s = (uint32_t)(w >> 48);
                         }
                     }
-                    gw = (BIG && h < span) ? __ldg(a.wheel.gapw + (s >> 3)) >> (4 * (s & 7)) : 0u;
+                    gwi = s >> 3;
+                    gw = (BIG && h < span) ? __ldg(a.wheel.gapw + gwi) >> (4 * (s & 7)) : 0u;
                     need = false;
                 }
                 for (;;) {
@@ -692,10 +713,13 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                         wb[wcnt + __popc(mask & lanemask_lt())] = v;
                         atomicAdd(&sh.hist[v >> bt], 1u);
                         if (BIG) {
+                            // gaps are 1..11, never 0: an empty word means all 8 are used
                             h += (uint64_t)(gw & 15u) * p;
                             gw >>= 4;
-                            if (++s == kBigCycle) s = 0;
-                            if ((s & 7) == 0) gw = __ldg(a.wheel.gapw + (s >> 3));
+                            if (gw == 0) {
+                                gwi = gwi + 1 == kBigWords ? 0u : gwi + 1;
+                                gw = __ldg(a.wheel.gapw + gwi);
+                            }
                         } else {
                             h += (uint64_t)wheel_gap(s) * p;
                             s = (s + 1) & 7;
@@ -705,6 +729,9 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                 }
                 if (full) break;
                 // next hit relative to the next group (h < span + 11 p < 2^48 unless none)
+                // wheel position: the gaps left in the current word tell where it stands
+                // (a lane that emitted nothing loaded no word and kept its position)
+                if (BIG && gw) s = 8 * gwi + 8 - ((32 - __clz(gw) + 3) >> 2);
                 if (idx < n) stw[idx] = ((unsigned long long)s << 48) | (h == kRunInf ? kRunInf : h - span);
                 lg += kScNW;
                 need = true;
@@ -815,7 +842,8 @@ __global__ void __launch_bounds__(1024) k_compact_scan(const uint32_t *block_cnt
 }
 
 __global__ void __launch_bounds__(kCpT) k_compact_write(const uint32_t *bits, uint64_t nwords, uint64_t jmax,
-                                                        const uint32_t *block_off, uint32_t *primes_out)
+                                                        const uint32_t *block_off, uint32_t *primes_out,
+                                                        uint64_t cap)
 {
     __shared__ uint32_t s_warp[33];
     const uint64_t w0 = ((uint64_t)blockIdx.x * kCpT + threadIdx.x) * kCpW;
@@ -832,7 +860,9 @@ __global__ void __launch_bounds__(kCpT) k_compact_write(const uint32_t *bits, ui
         while (x) {
             const uint32_t b = __ffs(x) - 1;
             x &= x - 1;
-            primes_out[pos++] = (uint32_t)(2 * (32 * (w0 + k) + b) + 1);
+            // never past the buffer: the host rejects a count above its capacity
+            if (pos < cap) primes_out[pos] = (uint32_t)(2 * (32 * (w0 + k) + b) + 1);
+            ++pos;
         }
     }
 }
@@ -844,13 +874,14 @@ cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStre
 }
 
 cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
-                           uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out, cudaStream_t st)
+                           uint32_t *block_off, uint32_t *primes_out, uint64_t cap, uint32_t *total_out,
+                           cudaStream_t st)
 {
     const uint64_t nwords = nbits / 32;
     const uint32_t nblocks = (uint32_t)((nwords + (uint64_t)kCpT * kCpW - 1) / ((uint64_t)kCpT * kCpW));
     k_compact_count<<<nblocks, kCpT, 0, st>>>(bits, nwords, jmax, block_cnt);
     k_compact_scan<<<1, 1024, 0, st>>>(block_cnt, nblocks, block_off, total_out);
-    if (primes_out) k_compact_write<<<nblocks, kCpT, 0, st>>>(bits, nwords, jmax, block_off, primes_out);
+    if (primes_out) k_compact_write<<<nblocks, kCpT, 0, st>>>(bits, nwords, jmax, block_off, primes_out, cap);
     return cudaGetLastError();
 }
 

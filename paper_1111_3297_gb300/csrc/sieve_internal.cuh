@@ -290,8 +290,9 @@ constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
 // run: the single-request kernel (every group one unit continuing the previous one)
 cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, bool run, cudaStream_t st);
 cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
+// primes_out holds cap entries; a count above cap writes only the first cap
 cudaError_t launch_compact(const uint32_t *bits, uint64_t nbits, uint64_t jmax, uint32_t *block_cnt,
-                           uint32_t *block_off, uint32_t *primes_out, uint32_t *total_out,
+                           uint32_t *block_off, uint32_t *primes_out, uint64_t cap, uint32_t *total_out,
                            cudaStream_t st);
 cudaError_t launch_barrett(const uint32_t *primes, uint64_t n, uint64_t *m, cudaStream_t st);
 cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc,
