@@ -76,6 +76,45 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
 // ---------------------------------------------------------------------------
 // tile kernel
 // ---------------------------------------------------------------------------
+
+// One pre-sieve pass over the tile's words: OR of the patterns of groups
+// [G0, G0 + NG) (Sec. 3.1).  Thread tid takes words tid, tid + T, ...; the
+// pattern window of group g for word w starts at rho = (J + 32 w) mod P_g.  The
+// first pass (G0 = 0) writes the words, a later one ORs into them; the last pass
+// also clears the bits of the small primes themselves (q = q * 1 is prime).
+template <int T, int G0, int NG>
+__device__ __forceinline__ void presieve_pass(uint32_t *sm, const TileArgs &a, const uint32_t *s_rho0,
+                                              uint32_t nwords, bool last, uint64_t J)
+{
+    const uint32_t tid = threadIdx.x;
+    uint32_t rho[NG];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+        // rho = (rho0 + 32 tid) mod P: the quotient estimated in float, corrected exactly
+        const uint32_t P = a.ps.modulus[G0 + k], x = 32u * tid;
+        const uint32_t q = __float2uint_rz(__uint2float_rn(x) * a.ps.inv[G0 + k]);
+        int32_t r = (int32_t)(x - q * P);
+        if (r < 0) r += (int32_t)P;
+        if (r >= (int32_t)P) r -= (int32_t)P;
+        const uint32_t r2 = s_rho0[G0 + k] + (uint32_t)r;
+        rho[k] = r2 >= P ? r2 - P : r2;
+    }
+    for (uint32_t w = tid; w < nwords; w += T) {
+        uint32_t mask = G0 ? sm[w] : 0u;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            const uint32_t r = rho[k];
+            mask |= (uint32_t)(__ldg(a.pat + a.ps.word_off[G0 + k] + (r >> 5)) >> (r & 31));
+            const uint32_t nr = r + a.ps.inc[G0 + k];
+            rho[k] = nr >= a.ps.modulus[G0 + k] ? nr - a.ps.modulus[G0 + k] : nr;
+        }
+        if (last) {
+            const uint64_t Jw = J + 32ull * w;
+            if (Jw < 64) mask &= ~(uint32_t)(kSmallPrimeBits >> Jw);
+        }
+        sm[w] = mask;
+    }
+}
 template <int T>
 __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
 {
@@ -103,49 +142,27 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
         const bool carried = a.run && it > 0;  // the previous tile of this CTA ends where d starts
 
         // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
-        // Two passes of up to 7 groups each (fewer live residues); the second
-        // pass ORs into the words the first one wrote.
+        // Passes of at most 7 groups (fewer live residues per thread), each compiled
+        // for its exact groups; the second pass ORs into the words the first wrote.
         if (tid < ng) s_rho0[tid] = mod_barrett(d.J, a.ps.modulus[tid], a.ps.barrett[tid]);
         __syncthreads();
-        constexpr int kPass = 7;
-#pragma unroll 1
-        for (int g0 = 0; g0 < (int)ng; g0 += kPass) {
-            uint32_t rho[kPass];
-#pragma unroll
-            for (int k = 0; k < kPass; ++k) {
-                const int g = g0 + k;
-                rho[k] = 0;
-                if (g < (int)ng) {
-                    // thread tid starts at word tid: rho = (rho0 + 32 tid) mod P, the
-                    // quotient estimated in float and corrected exactly
-                    const uint32_t P = a.ps.modulus[g], x = 32u * tid;
-                    const uint32_t q = __float2uint_rz(__uint2float_rn(x) * a.ps.inv[g]);
-                    int32_t r = (int32_t)(x - q * P);
-                    if (r < 0) r += (int32_t)P;
-                    if (r >= (int32_t)P) r -= (int32_t)P;
-                    const uint32_t r2 = s_rho0[g] + (uint32_t)r;
-                    rho[k] = r2 >= P ? r2 - P : r2;
-                }
-            }
-            for (uint32_t w = tid; w < nwords; w += T) {
-                uint32_t mask = g0 ? sm[w] : 0u;
-#pragma unroll
-                for (int k = 0; k < kPass; ++k) {
-                    const int g = g0 + k;
-                    if (g < (int)ng) {
-                        const uint32_t r = rho[k];
-                        mask |= (uint32_t)(__ldg(a.pat + a.ps.word_off[g] + (r >> 5)) >> (r & 31));
-                        const uint32_t nr = r + a.ps.inc[g];
-                        rho[k] = nr >= a.ps.modulus[g] ? nr - a.ps.modulus[g] : nr;
-                    }
-                }
-                if (g0 + kPass >= (int)ng) {
-                    // last pass: a pattern also marks each small prime q = q*1 itself
-                    const uint64_t Jw = d.J + 32ull * w;
-                    if (Jw < 64) mask &= ~(uint32_t)(kSmallPrimeBits >> Jw);
-                }
-                sm[w] = mask;
-            }
+        switch (ng < 7 ? ng : 7) {
+        case 1: presieve_pass<T, 0, 1>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        case 2: presieve_pass<T, 0, 2>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        case 3: presieve_pass<T, 0, 3>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        case 4: presieve_pass<T, 0, 4>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        case 5: presieve_pass<T, 0, 5>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        case 6: presieve_pass<T, 0, 6>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        default: presieve_pass<T, 0, 7>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
+        }
+        switch (ng > 7 ? ng - 7 : 0) {
+        case 0: break;
+        case 1: presieve_pass<T, 7, 1>(sm, a, s_rho0, nwords, true, d.J); break;
+        case 2: presieve_pass<T, 7, 2>(sm, a, s_rho0, nwords, true, d.J); break;
+        case 3: presieve_pass<T, 7, 3>(sm, a, s_rho0, nwords, true, d.J); break;
+        case 4: presieve_pass<T, 7, 4>(sm, a, s_rho0, nwords, true, d.J); break;
+        case 5: presieve_pass<T, 7, 5>(sm, a, s_rho0, nwords, true, d.J); break;
+        default: presieve_pass<T, 7, 6>(sm, a, s_rho0, nwords, true, d.J); break;
         }
         __syncthreads();
 
@@ -634,6 +651,32 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kRunInf = (1ull << 48) - 1;
 
+// One wheel step of a large prime: the next struck multiple.  Mod-15015 wheel:
+// gw holds the unused gaps (4 bits each, 1..11, never 0) of gap word gwi, so an
+// empty word means all 8 are used; mod-15 wheel: s is the cycle position.
+template <bool BIG>
+__device__ __forceinline__ void scatter_step(uint64_t &h, uint32_t &s, uint32_t &gw, uint32_t &gwi, uint32_t p,
+                                             const uint32_t *gapw)
+{
+    if (BIG) {
+        h += (uint64_t)(gw & 15u) * p;
+        gw >>= 4;
+        if (gw == 0) {
+            gwi = gwi + 1 == kBigWords ? 0u : gwi + 1;
+            gw = __ldg(gapw + gwi);
+        }
+    } else {
+        h += (uint64_t)wheel_gap(s) * p;
+        s = (s + 1) & 7;
+    }
+}
+
+// mod-15015 cycle position of a prime whose gap word gwi has the gaps gw left
+__device__ __forceinline__ uint32_t big_wheel_pos(uint32_t gw, uint32_t gwi)
+{
+    return 8 * gwi + 8 - ((32 - __clz(gw) + 3) >> 2);
+}
+
 template <bool BIG>
 __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
 {
@@ -642,6 +685,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
     __shared__ uint32_t s_warp[33];
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
     const ChunkDesc ch = a.chunks[blockIdx.x];
     const uint32_t n = ch.p_hi - ch.p_lo;  // every group covers the chunk's primes
     const uint32_t nlg = (n + 31) / 32;
@@ -659,16 +703,17 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         const uint32_t jsx = first ? (BIG ? (uint32_t)(u.J % kBigW) : (uint32_t)(u.J % 15u)) : 0u;
         scatter_group_setup(a, g, sh);
 
-        // the current lane group's state and the next one's words, loaded ahead
+        // the lane group's prime and state (one prime per lane)
         uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0, gwi = 0;
-        uint64_t h = kRunInf;
-        bool need = true;
+        uint64_t h = 0;
+        // the next lane group's words, loaded ahead
         uint32_t p_n = 0;
         unsigned long long w_n = 0;
         if (lg < nlg) {
             p_n = pr[lg * 32 + lane];
             if (!first) w_n = stw[lg * 32 + lane];
         }
+        bool need = true;
         for (;;) {
             uint32_t wcnt = 0;
             bool full = false;
@@ -710,36 +755,23 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                     }
                     if (act) {
                         const uint32_t v = ebase + (uint32_t)h;
-                        wb[wcnt + __popc(mask & lanemask_lt())] = v;
+                        wb[wcnt + __popc(mask & lt)] = v;
                         atomicAdd(&sh.hist[v >> bt], 1u);
-                        if (BIG) {
-                            // gaps are 1..11, never 0: an empty word means all 8 are used
-                            h += (uint64_t)(gw & 15u) * p;
-                            gw >>= 4;
-                            if (gw == 0) {
-                                gwi = gwi + 1 == kBigWords ? 0u : gwi + 1;
-                                gw = __ldg(a.wheel.gapw + gwi);
-                            }
-                        } else {
-                            h += (uint64_t)wheel_gap(s) * p;
-                            s = (s + 1) & 7;
-                        }
+                        scatter_step<BIG>(h, s, gw, gwi, p, a.wheel.gapw);
                     }
                     wcnt += __popc(mask);
                 }
                 if (full) break;
                 // next hit relative to the next group (h < span + 11 p < 2^48 unless none)
-                // wheel position: the gaps left in the current word tell where it stands
-                // (a lane that emitted nothing loaded no word and kept its position)
-                if (BIG && gw) s = 8 * gwi + 8 - ((32 - __clz(gw) + 3) >> 2);
+                // with the wheel position (a lane that emitted nothing kept its own)
+                if (BIG && gw) s = big_wheel_pos(gw, gwi);
                 if (idx < n) stw[idx] = ((unsigned long long)s << 48) | (h == kRunInf ? kRunInf : h - span);
                 lg += kScNW;
                 need = true;
             }
-            const bool more = lg < nlg;
             __syncthreads();
             scatter_flush(a, g, sh, wb, wcnt, s_warp);
-            if (!__syncthreads_or(more)) break;
+            if (!__syncthreads_or(lg < nlg)) break;
         }
     }
 }
