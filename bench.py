@@ -414,8 +414,11 @@ def main():
     n_tile = prof["launches"][S.K_TILE] / steps
     n_scatter = prof["launches"][S.K_SCATTER] / steps
     marks = h_medium + h_large
+    # tile: table written once, each bucket entry read once; scatter (one interval):
+    # each bucket entry written once, and per prime and scatter group the prime (4 B)
+    # and its 8-byte state word read and written back
     tile_bytes = N / 8 + 4 * h_large
-    scatter_bytes = 4 * h_large + 12 * prof["prime_reads"] / steps
+    scatter_bytes = 4 * h_large + 20 * prof["prime_reads"] / steps
     kernels = {
         "k_tile": {"ms_per_step": t_tile * 1e3, "launches_per_step": n_tile,
                    "marks": marks, "atomics_per_s": marks / t_tile if t_tile else None,
