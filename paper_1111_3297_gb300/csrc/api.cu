@@ -807,7 +807,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
         ta.barrett = d_boot_m;
         ta.med_lo = med_lo;
         ta.coop_hi = (uint32_t)(std::upper_bound(boot.begin(), boot.end(), 1u << 13) - boot.begin());
-        ta.blk_hi = std::max(med_lo, (uint32_t)(std::upper_bound(boot.begin(), boot.end(), (uint32_t)(B / (60 * 32))) - boot.begin()));
+        ta.blk_hi = std::max(med_lo, (uint32_t)(std::upper_bound(boot.begin(), boot.end(), (uint32_t)(B / (240 * 32))) - boot.begin()));
         ta.pat = c->d_pat;
         ta.ps.ngroups = kMaxPresieveGroups;
         for (int g = 0; g < kMaxPresieveGroups; ++g) {

@@ -173,11 +173,10 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
         const uint32_t js15 = (uint32_t)(d.J % 15u);
         const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
         {
-            // smallest primes: every warp takes every prime, but only strikes inside
-            // its own slice of the tile (the work of one prime is spread over the CTA)
+            // smallest primes: every warp takes every prime and strikes every NW-th
+            // step of it (warp w: steps w, w + NW, ...), so the work of one prime is
+            // spread over the whole CTA and a warp's start is one multiply-add
             constexpr uint32_t NW = T / 32;
-            const uint32_t sl = ((len + NW - 1) / NW + 31) & ~31u;
-            const uint32_t S0 = min(len, warp * sl), E0 = min(len, S0 + sl);
             const uint32_t blk_end = min(a.blk_hi, d.med_hi);
             for (uint32_t b = a.med_lo; b < blk_end; b += 32) {
                 const uint32_t idx = b + lane;
@@ -191,21 +190,14 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                     const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
                     const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
                     const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
-                    if (hj >= E0) continue;
-                    const uint32_t step = 60u * pj;
-                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
-                    if (pos < S0) {
-                        // skip to the first step at or after the slice start: the quotient
-                        // estimated in float, then corrected exactly
-                        const uint32_t d = S0 - pos;
-                        uint32_t k = __float2uint_rz(__uint2float_rn(d) * __frcp_rn(__uint2float_rn(step)));
-                        pos += k * step;
-                        while (pos < S0) pos += step;
-                        while (pos >= S0 + step) pos -= step;
-                    }
-                    while (pos < E0) {
+                    if (hj >= len) continue;
+                    // the host gives this phase primes with 4 * NW steps <= the tile, so
+                    // pos stays below len + NW * step < 2^21
+                    const uint32_t step = 60u * pj, stride = NW * step;
+                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj + warp * step;
+                    while (pos < len) {
                         atomicOr(&sm[pos >> 5], 1u << (pos & 31));
-                        pos += step;
+                        pos += stride;
                     }
                 }
             }
@@ -268,11 +260,16 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                     else
                         mn = a.barrett[nidx];
                 }
+                // next hit offset in the tile, or kNone when at or beyond len + 2^29 - 1
+                // (medium primes < 2^28: every offset below fits 32 bits)
+                constexpr uint32_t kNone = 0xFFFFFFFFu;
                 uint32_t s = cc >> 29;
-                uint64_t hh = (cc & 0x1FFFFFFFu) == 0x1FFFFFFFu ? kStateInf : (cc & 0x1FFFFFFFu);
-                if (!carried) hh = first_hit(d.J, js15, p, m, s);
-                if (hh < len) {
-                    uint32_t h = (uint32_t)hh;
+                uint32_t h = (cc & 0x1FFFFFFFu) == 0x1FFFFFFFu ? kNone : (cc & 0x1FFFFFFFu);
+                if (!carried) {
+                    const uint64_t f = first_hit(d.J, js15, p, m, s);
+                    h = f < (uint64_t)len + 0x1FFFFFFFu ? (uint32_t)f : kNone;
+                }
+                if (h < len) {
                     // gaps of the mod-15 wheel from state s on, 2 bits each: the packed
                     // cycle doubled to 32 bits, so a rotate by 2 is one wheel step
                     uint32_t gq = __funnelshift_r(kGapPacked * 0x10001u, kGapPacked * 0x10001u, 2 * s), k = 0;
@@ -284,12 +281,11 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
                         if (h >= len) break;
                     }
                     s = (s + k) & 7;
-                    hh = h;
                 }
                 if (a.run) {
                     // next hit relative to the next tile; all ones (kept as is) when it
                     // lies beyond the run, which spans less than 2^29 - 1 bits
-                    const uint32_t off = hh >= (uint64_t)len + 0x1FFFFFFFull ? 0x1FFFFFFFu : (uint32_t)(hh - len);
+                    const uint32_t off = h >= len + 0x1FFFFFFFu ? 0x1FFFFFFFu : h - len;
                     ch[idx] = (s << 29) | off;
                 }
                 idx = nidx;
