@@ -426,7 +426,14 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
         grp_open = false;
     };
 
-    for (size_t r = 0; r < reqs.size(); ++r) {
+    // requests in order of decreasing magnitude: a scatter group then holds requests
+    // that need about the same large primes, and chunks of primes above a group's
+    // largest skip it (outputs do not depend on the order: every tile has its own
+    // output offset and request index)
+    std::vector<size_t> order(reqs.size());
+    for (size_t r = 0; r < reqs.size(); ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return info[x].plimit > info[y].plimit; });
+    for (size_t r : order) {
         const ReqSpec &q = reqs[r];
         const ReqInfo &ri = info[r];
         const bool large = ri.large_hi > large_lo;
@@ -480,6 +487,7 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
                     u.span = d.len;
                     u.tile_rel = rel;
                     u.plimit = ri.plimit;
+                    u.jw = (uint32_t)(d.J % (P->big_wheel ? kBigW : 15u));
                     P->sus.push_back(u);
                     grp.nsu++;
                 }

@@ -575,9 +575,15 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                             s = (uint32_t)(cs >> 32);
                         }
                     } else if (p != 0 && p <= u.plimit) {
-                        const uint64_t hh = BIG ? first_hit_big(u.J, (uint32_t)(u.J % kBigW), p, m, a.wheel, s)
-                                                : first_hit(u.J, (uint32_t)(u.J % 15u), p, m, s);
-                        if (hh < kStateInf) h = (uint32_t)hh;
+                        // a first multiple already past the unit means no hit in it (the
+                        // p^2 start and the wheel only move it later), unless the next hit
+                        // has to be carried into the next group
+                        const uint32_t q = lemma_q(u.J, p, m);
+                        if (q < u.span || (su + 1 == su_end && g.carry_out)) {
+                            const uint64_t hh = BIG ? first_hit_big_q(u.J, u.jw, p, q, a.wheel, s)
+                                                    : first_hit_q(u.J, u.jw, p, q, s);
+                            if (hh < kStateInf) h = (uint32_t)hh;
+                        }
                     }
                     gw = BIG ? __ldg(a.wheel.gapw + (s >> 3)) >> (4 * (s & 7)) : 0u;
                     need_hit = false;
@@ -696,7 +702,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         const SUDesc u = a.sus[g.su0];
         const bool first = a.run_first && gi == 0;
         const uint32_t span = u.span, ebase = u.tile_rel << bt;
-        const uint32_t jsx = first ? (BIG ? (uint32_t)(u.J % kBigW) : (uint32_t)(u.J % 15u)) : 0u;
+        const uint32_t jsx = u.jw;
         scatter_group_setup(a, g, sh);
 
         // the lane group's prime and state (one prime per lane)

@@ -100,12 +100,18 @@ __device__ __forceinline__ uint32_t mod_barrett(uint64_t x, uint32_t p, uint64_t
 //   * Sec. 1.4: striking with p starts at p^2, whose index is (p^2-1)/2.
 //   * Sec. 3.2.1: then advance to the first multiple p*c with c coprime to 15.
 // js15 = Js mod 15.  Returns h as 64-bit (the p^2 start can lie far ahead).
-__device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32_t p, uint64_t m,
-                                              uint32_t &state)
+// Lemma lem:q: offset of the first J >= Js with p | 2J+1
+__device__ __forceinline__ uint32_t lemma_q(uint64_t Js, uint32_t p, uint64_t m)
 {
-    uint32_t r = mod_barrett(Js, p, m);
-    uint32_t half = p >> 1;
-    uint32_t q = (r <= half) ? (half - r) : (half + (p - r));
+    const uint32_t r = mod_barrett(Js, p, m);
+    const uint32_t half = p >> 1;
+    return (r <= half) ? (half - r) : (half + (p - r));
+}
+
+// the rest of first_hit once q = lemma_q(Js, p, m) is known
+__device__ __forceinline__ uint64_t first_hit_q(uint64_t Js, uint32_t js15, uint32_t p, uint32_t q,
+                                                uint32_t &state)
+{
     uint64_t jsq = ((uint64_t)p * p) >> 1;  // (p^2 - 1) / 2, p odd
     uint64_t h;
     uint32_t c15;
@@ -122,6 +128,12 @@ __device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32
     uint32_t sk = (kSkipPacked >> (2 * c15)) & 3u;
     state = (uint32_t)(kStateAfterPacked >> (3 * c15)) & 7u;
     return h + (uint64_t)sk * p;
+}
+
+__device__ __forceinline__ uint64_t first_hit(uint64_t Js, uint32_t js15, uint32_t p, uint64_t m,
+                                              uint32_t &state)
+{
+    return first_hit_q(Js, js15, p, lemma_q(Js, p, m), state);
 }
 
 // ---------------------------------------------------------------------------
@@ -144,13 +156,10 @@ struct BigWheel {
     const uint16_t *inv;
 };
 
-// As first_hit, with the mod-15015 wheel; jsw = Js mod 15015.
-__device__ __forceinline__ uint64_t first_hit_big(uint64_t Js, uint32_t jsw, uint32_t p, uint64_t m,
-                                                  const BigWheel &w, uint32_t &state)
+// As first_hit_q, with the mod-15015 wheel; jsw = Js mod 15015.
+__device__ __forceinline__ uint64_t first_hit_big_q(uint64_t Js, uint32_t jsw, uint32_t p, uint32_t q,
+                                                    const BigWheel &w, uint32_t &state)
 {
-    uint32_t r = mod_barrett(Js, p, m);
-    uint32_t half = p >> 1;
-    uint32_t q = (r <= half) ? (half - r) : (half + (p - r));
     uint64_t jsq = ((uint64_t)p * p) >> 1;
     uint64_t h;
     uint32_t cw;
@@ -166,6 +175,12 @@ __device__ __forceinline__ uint64_t first_hit_big(uint64_t Js, uint32_t jsw, uin
     const uint32_t e = __ldg(w.rstate + cw);
     state = e & 0xFFFFu;
     return h + (uint64_t)(e >> 16) * p;
+}
+
+__device__ __forceinline__ uint64_t first_hit_big(uint64_t Js, uint32_t jsw, uint32_t p, uint64_t m,
+                                                  const BigWheel &w, uint32_t &state)
+{
+    return first_hit_big_q(Js, jsw, p, lemma_q(Js, p, m), w, state);
 }
 
 // ---------------------------------------------------------------------------
@@ -206,7 +221,7 @@ struct SUDesc {         // scatter unit: consecutive tiles of one request inside
     uint32_t span;      // bits covered (<= 2^30)
     uint32_t tile_rel;  // index of its first tile relative to the group's first tile
     uint32_t plimit;    // largest prime that may strike (isqrt of the request's last number)
-    uint32_t pad;
+    uint32_t jw;        // J mod W of the plan's large-prime wheel (15 or 15015)
 };
 static_assert(sizeof(SUDesc) == 24, "SUDesc layout");
 
