@@ -166,6 +166,8 @@ typedef struct {
 /* Tuning classes: by the magnitude of the interval's largest number. */
 #define SIEVE_TUNE_CLASSES 4 /* < 2^40, < 2^50, < 2^56, >= 2^56 */
 sieve_status sieve_get_tuning(sieve_ctx *ctx, uint32_t cls, sieve_tuning *out);
+/* Replaces the tuning of class cls (SIEVE_EINVAL if out of range); it also drops a
+ * tuning sieve_autotune_batch stored, so batches follow the classes again. */
 sieve_status sieve_set_tuning(sieve_ctx *ctx, uint32_t cls, const sieve_tuning *in);
 
 /*
@@ -180,7 +182,8 @@ sieve_status sieve_autotune(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
  * Autotune the batched form on a request list (as for sieve_batch): time candidate
  * tile sizes (2^16..2^20 bits), medium/large thresholds and windows on the
  * actual requests, writing dev_arena / dev_counts as sieve_batch would; the
- * fastest becomes the tuning sieve_batch uses from then on.  Waits for the device.
+ * fastest becomes the tuning sieve_batch uses from then on (until the next
+ * sieve_set_tuning).  Waits for the device.
  */
 sieve_status sieve_autotune_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t count,
                                   uint32_t *dev_arena, uint64_t *dev_counts, sieve_tuning *out,

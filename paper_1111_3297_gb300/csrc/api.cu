@@ -1177,6 +1177,7 @@ sieve_status sieve_set_tuning(sieve_ctx *c, uint32_t cls, const sieve_tuning *in
 {
     if (!c || !in || cls >= SIEVE_TUNE_CLASSES || !tuning_valid(*in)) return SIEVE_EINVAL;
     c->tune[cls] = *in;
+    c->batch_tune = sieve_tuning{};  // an explicit tuning replaces the autotuned batch one
     return SIEVE_OK;
 }
 

@@ -158,3 +158,39 @@ def test_serving_results_equal_alone_and_in_the_mix(ctx):
             assert results[rid][1] == sha(plain)
     finally:
         srv.close()
+
+
+def test_batch_with_epochs_longer_than_2p32_bits(ctx):
+    """Two long requests through the multi-request scatter with epochs of 8192 tiles of
+    2^20 bits (2^33 bits): the next hits carried between its groups are 32-bit offsets,
+    so there it must recompute first hits per group instead; the tables must equal the
+    single-interval path bit for bit and Miller-Rabin on sampled bits."""
+    import oracle
+    saved = [S.sieve_get_tuning(ctx, k) for k in range(4)]
+    try:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, tile_log2=20, presieve_groups=2, coop_max=4096,
+                               medium_max=1 << 20, window_tiles=1024, epoch_tiles=8192)
+        nb = 1 << 33
+        reqs = [(2 ** 46, nb), (3 * 2 ** 47 + (1 << 20), nb)]
+        lay, off = layout(reqs, 4)
+        arena = torch.empty(off, dtype=torch.int32, device="cuda")
+        counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
+        S.sieve_batch(ctx, lay, arena, counts)
+        S.sieve_sync(ctx)
+        rng = workloads.SplitMix64(46)
+        for (j0, n, o), c in zip(lay, counts.cpu().tolist()):
+            plain = torch.empty(n // 32, dtype=torch.int32, device="cuda")
+            S.sieve_segments(ctx, 5, j0 // 32, n // 32, plain)
+            S.sieve_sync(ctx)
+            got = arena[o:o + n // 32]
+            assert torch.equal(got, plain), "request at j0=%d differs from the single-interval path" % j0
+            assert c == S.sieve_count(ctx, plain, n)
+            for _ in range(400):
+                j = rng.below(n)
+                word = int(got[j // 32].item()) & 0xFFFFFFFF
+                assert ((word >> (j % 32)) & 1) == (0 if oracle.is_prime_mr(2 * (j0 + j) + 1) else 1), (j0, j)
+            del plain
+    finally:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **saved[k])
