@@ -193,6 +193,16 @@ def cpu_baseline(wl, f):
                       % (sample, n, l, dt, cores)}
 
 
+def kernel_code_hash(path):
+    """SHA-256 (16 hex digits) of a CUDA source with comments and blank lines removed:
+    the key under which profiles/traffic.json stores counters of that code."""
+    import hashlib
+    import re
+    src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.split("\n")]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
+
+
 def measure_batch(S, ctx, args, rank, world):
     """4096 seeded requests of uneven length (2^16..2^28 numbers) and magnitude
     (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
@@ -429,15 +439,13 @@ def main():
     }
     # DRAM traffic per launch from the committed ncu capture of the same kernel on a
     # smaller slice of the same workload, scaled by the kernel's units per launch;
-    # null when kernels.cu changed since the capture
+    # null when the code of kernels.cu changed since the capture
     traffic = {"k_tile": None, "k_scatter": None}
     try:
-        import hashlib
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ksha = hashlib.sha256(open(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc", "kernels.cu"),
-                                   "rb").read()).hexdigest()[:16]
+        ksha = kernel_code_hash(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc", "kernels.cu"))
         key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload)
-        if key and tj.get("kernels_cu_sha256_16") == ksha and key in tj:
+        if key and tj.get("kernels_cu_code_sha256_16") == ksha and key in tj:
             tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
             if n_tile:
                 traffic["k_tile"] = tt["dram_bytes"] / tt["units"] * (N / n_tile)

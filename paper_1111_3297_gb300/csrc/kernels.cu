@@ -5,10 +5,12 @@
 //                through shared memory with the mod-15 wheel (Sec. 2.1, Sec. 3.2.1),
 //                drain of the tile's large-prime bucket (Sec. 2.2-2.3), coalesced
 //                128-bit store and popcount.
-//   k_scatter    large primes (stride beyond the tile): first hit by Barrett reduction
-//                (Lemma lem:q, Sec. 1.4), all hits of a window staged in shared memory
-//                per warp, counting-sorted by tile and appended to per-tile buckets in
-//                HBM with one atomic reservation per (tile, flush).
+//   k_scatter_run, k_scatter   large primes (stride beyond the tile) into per-tile
+//                buckets in HBM: hits staged per warp in shared memory, counting-sorted
+//                by tile, appended with one atomic reservation per (tile, flush).  One
+//                interval: each prime's next hit and wheel position live in one state
+//                word through the whole interval.  Several requests: first hit per
+//                (prime, request unit) by Barrett reduction (Lemma lem:q, Sec. 1.4).
 //   k_bootstrap, k_compact_*, k_barrett   the base of Sec. 1.4 built on the device.
 //   k_popcount   composite count of a table.
 //   k_probe_smem shared-memory atomic-OR rate (roofline denominator).
@@ -399,10 +401,11 @@ int tile_blocks_per_sm(uint32_t tile_log2)
 // chunks carry similar work), walked through every scatter group of the epoch
 // (a group is <= kScatterMaxTiles tiles of one or more requests).  Prime-major: a
 // warp takes 32 primes (one per lane, prime and Barrett constant in registers),
-// walks the group's scatter units, computes each unit's first hit (Lemma lem:q,
-// the p^2 start of Sec. 1.4, the mod-15015 or mod-15 wheel) and emits every hit of the
-// unit into its own staging buffer in shared memory, counting hits per tile as
-// it goes.  When a warp's buffer is full the CTA flushes: block scan of the
+// walks the group's scatter units (k_scatter: one per request run in the group;
+// k_scatter_run: the single unit of an interval), finds each unit's first hit
+// (Lemma lem:q, the p^2 start of Sec. 1.4, the mod-15015 or mod-15 wheel) and
+// emits every hit of the unit into its warp's staging buffer in shared memory,
+// counting hits per tile as it goes.  When a warp's buffer is full the CTA flushes: block scan of the
 // per-tile counts, one atomic reservation per (tile, flush) in the tile's
 // bucket (issued before the sort, consumed after it), each warp counting-sorts
 // its own entries, and a store pass in which
