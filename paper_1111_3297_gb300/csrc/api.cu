@@ -288,15 +288,17 @@ sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoc
 // Requests whose largest prime exceeds medium_max also get large-prime
 // buckets: their tiles are grouped into scatter groups (<= window_tiles tiles,
 // runs of one request form a scatter unit) and groups into epochs whose bucket
-// capacity fits the pool.  Per epoch: scatter launch, then tile launch.
-// Scatter chunks: each CTA takes a run of large primes of one group.  Runs are
-// cut so that every chunk of an epoch carries about the same estimated work: a
-// first-hit computation per (prime, scatter unit) plus the prime's hits, which
-// number span*(8/15)/p (the wheel keeps 8 of 15 multiples).  Small large primes
-// have many hits each, so their chunks hold few primes.
+// capacity fits the pool.  Per epoch: scatter launch, then tile launch (the
+// scatter of the next epoch may overlap it, on the other bucket pool).
+// Scatter chunks: each CTA takes a run of large primes through every group of
+// the epoch.  Runs are cut so that every chunk of an epoch carries about the
+// same estimated work: a visit per (prime, scatter unit) plus the prime's hits,
+// which number span*density/p (density 8/15 or 5760/15015, the share of
+// multiples the wheel keeps).  Small large primes have many hits each, so their
+// chunks hold few primes.
 static void make_chunks(sieve_ctx *c, Plan *P)
 {
-    const double kFirstHitCost = 2.0;  // one first hit ~ two emitted hits
+    const double kFirstHitCost = 2.0;  // one visit ~ two emitted hits
     for (Plan::Epoch &e : P->epochs) {
         e.c0 = (uint32_t)P->chunks.size();
         e.nc = 0;

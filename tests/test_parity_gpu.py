@@ -247,3 +247,19 @@ def test_top_of_range_against_miller_rabin():
             assert bit == (0 if oracle.is_prime_mr(2 * (j0 + j) + 1) else 1), j
     finally:
         c.close()
+
+
+def test_segments_larger_than_a_tile_equal_small_segments(ctx):
+    """The table depends only on the numbers, not on l (Sec. 1.3): two segments of
+    l = 30 (each 1024 on-chip tiles) equal 2048 segments of l = 20 over the same
+    numbers, bit for bit, and Miller-Rabin on sampled bits."""
+    f30 = 9311  # numbers around 2^42 * 2 ~ 1.8e13
+    big = run_plain(ctx, 30, f30, 2)
+    small = run_plain(ctx, 20, f30 << 10, 2048)
+    assert torch.equal(big, small)
+    rng = workloads.SplitMix64(30)
+    J0 = f30 << 30
+    for _ in range(500):
+        j = rng.below(2 << 30)
+        bit = (int(big[j // 32].item()) >> (j % 32)) & 1
+        assert bit == (0 if oracle.is_prime_mr(2 * (J0 + j) + 1) else 1), j
