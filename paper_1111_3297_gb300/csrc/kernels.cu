@@ -566,30 +566,47 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter(ScatterArgs a)
                     }
                     need_load = false;
                 }
-                const SUDesc u = a.sus[su];
+                SUDesc u;
                 if (need_hit) {
-                    h = kStateInf;
-                    s = 0;
+                    // first hits unit after unit; a unit in which no lane's prime has a
+                    // hit (the common case: units shorter than the primes) is passed
+                    // over here, without the emit path
                     const uint32_t idx = lg * 32 + lane;
-                    if (su == g.su0 && g.carry_in) {
-                        // continue from where this prime left the previous group
-                        if (idx < n) {
-                            h = (uint32_t)cs;
-                            s = (uint32_t)(cs >> 32);
+                    for (;;) {
+                        u = a.sus[su];
+                        const bool cout = su + 1 == su_end && g.carry_out;
+                        h = kStateInf;
+                        s = 0;
+                        if (su == g.su0 && g.carry_in) {
+                            // continue from where this prime left the previous group
+                            if (idx < n) {
+                                h = (uint32_t)cs;
+                                s = (uint32_t)(cs >> 32);
+                            }
+                        } else if (p != 0 && p <= u.plimit) {
+                            // a first multiple already past the unit means no hit in it (the
+                            // p^2 start and the wheel only move it later), unless the next
+                            // hit has to be carried into the next group
+                            const uint32_t q = lemma_q(u.J, p, m);
+                            if (q < u.span || cout) {
+                                const uint64_t hh = BIG ? first_hit_big_q(u.J, u.jw, p, q, a.wheel, s)
+                                                        : first_hit_q(u.J, u.jw, p, q, s);
+                                if (hh < kStateInf) h = (uint32_t)hh;
+                            }
                         }
-                    } else if (p != 0 && p <= u.plimit) {
-                        // a first multiple already past the unit means no hit in it (the
-                        // p^2 start and the wheel only move it later), unless the next hit
-                        // has to be carried into the next group
-                        const uint32_t q = lemma_q(u.J, p, m);
-                        if (q < u.span || (su + 1 == su_end && g.carry_out)) {
-                            const uint64_t hh = BIG ? first_hit_big_q(u.J, u.jw, p, q, a.wheel, s)
-                                                    : first_hit_q(u.J, u.jw, p, q, s);
-                            if (hh < kStateInf) h = (uint32_t)hh;
+                        if (cout || __any_sync(0xffffffffu, h < u.span)) break;
+                        if (++su == su_end) {
+                            su = g.su0;
+                            lg += kScNW;
+                            need_load = true;
+                            break;
                         }
                     }
+                    if (need_load) continue;
                     gw = BIG ? __ldg(a.wheel.gapw + (s >> 3)) >> (4 * (s & 7)) : 0u;
                     need_hit = false;
+                } else {
+                    u = a.sus[su];
                 }
                 const uint32_t ebase = u.tile_rel << bt;
                 for (;;) {
