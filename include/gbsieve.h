@@ -143,16 +143,20 @@ sieve_status sieve_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t co
                          uint32_t *dev_arena, uint64_t *dev_counts, sieve_stream stream);
 
 /*
- * Tuning of the device path (none of it changes the bits):
+ * Tuning of the device path (none of it changes the bits); sieve_set_tuning
+ * returns SIEVE_EINVAL outside these ranges:
  *   tile_log2     on-chip segment size 2^tile_log2 bits (12..20), one CTA per tile;
  *   presieve_groups  how many small-prime pattern groups pre-sieve a tile
  *                 (1..13; group 1 = {3,5,7,11,13}, up to 127 with 13 groups);
- *   coop_max      primes below this are struck by a whole warp, 32 multiples at a time;
- *   medium_max    primes up to this are struck inside the tile kernel; larger
- *                 primes go through the large-prime buckets;
- *   window_tiles  tiles per bucket window (scatter flush domain), 16..1024;
- *   epoch_tiles   tiles whose buckets are filled by one scatter pass (multiple of
- *                 window_tiles, bounded by the memory budget).
+ *   coop_max      primes up to this are struck by a whole warp, 32 multiples at a
+ *                 time (the smallest of them, up to 2^tile_log2 / (240 * warps), by
+ *                 the whole CTA); larger ones by one thread each;
+ *   medium_max    primes up to this (at most 2^28) are struck inside the tile
+ *                 kernel; larger primes go through the large-prime buckets;
+ *   window_tiles  tiles per scatter group (the flush domain of the bucket
+ *                 scatter), 1..1024, at most 2^30 bits;
+ *   epoch_tiles   tiles whose buckets one scatter launch fills (window_tiles..65535;
+ *                 an epoch also ends where the bucket pool is full).
  */
 typedef struct {
     uint32_t tile_log2;
