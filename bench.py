@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 1e12..1e18 midpoint sweep")
     return ap.parse_args()
 
 
@@ -135,6 +136,30 @@ def wheel_marks(J0, N, primes):
     return int(cnt[ok].sum())
 
 
+PRESIEVE_MAX = [13, 23, 31, 41, 47, 59, 67, 73, 83, 97, 103, 109, 127]  # largest prime of groups 1..13
+
+
+def medium_marks(J0, N, tune):
+    """Wheel-reduced marks of the primes the tile kernel strikes on [J0, J0+N): above
+    the pre-sieve's primes, up to medium_max and isqrt of the last number."""
+    import numpy as np
+    plimit = int(np.floor(np.sqrt(float(2 * (J0 + N) - 1))))
+    top = min(plimit, tune["medium_max"])
+    primes = base_primes_upto(top)
+    medium = primes[(primes > PRESIEVE_MAX[tune["presieve_groups"] - 1]) & (primes <= top)]
+    return wheel_marks(J0, N, medium)
+
+
+def step_roofline(N, marks, h_large, visits, t_step, hbm_peak, r_atom):
+    """T_roof = max(B_alg / BW_HBM, H / R_atom), B_alg = N/8 + 16 H_large + 4 V, against
+    the measured step time."""
+    b_alg = N / 8 + 16 * h_large + 4 * visits
+    t_roof = max(b_alg / (hbm_peak * 1e9), marks / r_atom)
+    return {"t_roof_ms": t_roof * 1e3, "t_step_ms": t_step * 1e3, "frac": t_roof / t_step,
+            "bytes_alg": b_alg, "marks": marks,
+            "bound": "hbm" if b_alg / (hbm_peak * 1e9) >= marks / r_atom else "smem_atomic"}
+
+
 def base_primes_upto(x):
     import numpy as np
     x = int(x)
@@ -201,6 +226,46 @@ def kernel_code_hash(path):
     src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
     lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.split("\n")]
     return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
+
+
+def measure_sweep(S, ctx, hbm_peak, r_atom):
+    """The paper's Table 1 workload (Sec. 5): one interval of 2^30 bits (l = 20,
+    n = 1024) with its midpoint at 10^e, e = 12..18, each timed alone (CUDA events,
+    5 calls after 3 warm-up calls, class tunings of the context) with its step
+    roofline."""
+    import torch
+    l, n = 20, 1024
+    N = n << l
+    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    points = []
+    for e in range(12, 19):
+        f = S.sieve_f_from_midpoint(l, n, 1, e)
+        J0 = f << l
+        for _ in range(3):
+            S.sieve_segments(ctx, l, f, n, out)
+        S.sieve_sync(ctx)
+        S.sieve_profile_enable(ctx, True)
+        S.sieve_profile_read(ctx)
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            S.sieve_segments(ctx, l, f, n, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = S.sieve_profile_read(ctx)
+        S.sieve_profile_enable(ctx, False)
+        t = e0.elapsed_time(e1) * 1e-3 / reps
+        vlast = 2 * (J0 + N - 1) + 1
+        tune = S.sieve_get_tuning(ctx, 0 if vlast < 2**40 else 1 if vlast < 2**50 else 2 if vlast < 2**56 else 3)
+        h_large = prof["large_hits"] / reps
+        roof = step_roofline(N, medium_marks(J0, N, tune) + h_large, h_large, prof["prime_reads"] / reps, t,
+                             hbm_peak, r_atom)
+        points.append({"midpoint": "1e%d" % e, "f": f, "ms": t * 1e3, "value": N / t,
+                       "step_roofline_frac": roof["frac"], "bound": roof["bound"]})
+    del out
+    return {"l": l, "n": n, "bits": N, "unit": "odd numbers/s", "points": points}
 
 
 def measure_batch(S, ctx, args, rank, world):
@@ -332,8 +397,8 @@ def main():
     J0 = f << l
     vmax = 2 * ((f0 + world * n) << l)
     # the batch and serving legs draw requests up to ~1e18
-    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 30)) if not (args.no_batch and args.no_serve)
-                       else vmax)
+    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 31))
+                       if not (args.no_batch and args.no_serve and args.no_sweep) else vmax)
     stream = torch.cuda.current_stream()
     out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
 
@@ -411,12 +476,7 @@ def main():
     tune = S.sieve_get_tuning(ctx, 0 if vmax < 2**40 else 1 if vmax < 2**50 else 2 if vmax < 2**56 else 3)
     if tuned:
         tune = tuned
-    import numpy as np
-    plimit = int(np.floor(np.sqrt(float(2 * (J0 + N) - 1))))
-    primes = base_primes_upto(min(plimit, tune["medium_max"]))
-    presieve_max = [13, 23, 31, 41, 47, 59, 67, 73, 83, 97, 103, 109, 127][tune["presieve_groups"] - 1]
-    medium = primes[(primes > presieve_max) & (primes <= min(plimit, tune["medium_max"]))]
-    h_medium = wheel_marks(J0, N, medium)  # per step
+    h_medium = medium_marks(J0, N, tune)  # per step
     steps = args.steps
     h_large = prof["large_hits"] / steps
     t_tile = prof["ms"][S.K_TILE] / steps * 1e-3
@@ -466,12 +526,11 @@ def main():
                 "frac": ach / hbm_peak, "traffic": traffic["k_scatter"],
                 "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
     # step-level roofline: the slower of HBM bytes at peak and marks at the atomic peak
-    step_s = ms_max * 1e-3 / steps
-    b_alg = N / 8 + 16 * h_large + 4 * prof["prime_reads"] / steps
-    t_roof = max(b_alg / (hbm_peak * 1e9), marks / r_atom)
-    step_roof = {"t_roof_ms": t_roof * 1e3, "t_step_ms": step_s * 1e3, "frac": t_roof / step_s,
-                 "bytes_alg": b_alg, "marks": marks, "bound": "hbm" if b_alg / (hbm_peak * 1e9) >= marks / r_atom
-                 else "smem_atomic"}
+    step_roof = step_roofline(N, marks, h_large, prof["prime_reads"] / steps, ms_max * 1e-3 / steps,
+                              hbm_peak, r_atom)
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = measure_sweep(S, ctx, hbm_peak, r_atom)
 
     base_line = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -497,7 +556,7 @@ def main():
             "gpu_launches": int(sum(prof["launches"])),
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "cpu_baseline": base_line, "e2e": e2e, "clocks": clk,
-            "batch": batch, "serving": serving,
+            "batch": batch, "serving": serving, "sweep": sweep,
             "composites": composites, "smem_atomic_peak_per_s": r_atom,
         }), flush=True)
     ctx.close()

@@ -162,17 +162,17 @@ uint32_t tune_class(uint64_t vlast)
     return lg < 40 ? 0 : lg < 50 ? 1 : lg < 56 ? 2 : 3;
 }
 
+// defaults near what the autotuner finds on GB300 for long intervals of each class
 sieve_tuning default_tuning(uint32_t cls)
 {
     sieve_tuning t;
     t.tile_log2 = 20;
-    t.presieve_groups = 6;
-    t.coop_max = 1u << 13;
-    t.medium_max = 1u << 20;
+    t.presieve_groups = 2;
+    t.coop_max = 1u << 12;
+    t.medium_max = cls >= 3 ? 1u << 19 : 1u << 20;
     t.window_tiles = 1024;
     t.epoch_tiles = 4096;
-    if (cls == 0) t.tile_log2 = 18, t.medium_max = 1u << 18, t.coop_max = 1u << 11;
-    return t;
+    return t;  // short intervals get smaller tiles from the planner (tuning_for)
 }
 
 bool tuning_valid(const sieve_tuning &t)
