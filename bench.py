@@ -437,6 +437,15 @@ def main():
     S.sieve_profile_enable(ctx, False)
     S.sieve_sync(ctx)
     ms_max = ms
+    # one more step (not timed) with the scatter and tile launches on one stream: each
+    # kernel's own time, whose shares compare with the ncu launch list and which picks
+    # the dominant kernel (inside the timed region the two overlap and share the SMs)
+    S.sieve_profile_enable(ctx, True, serial=True)
+    S.sieve_profile_read(ctx)
+    S.sieve_segments(ctx, l, f, n, out)
+    prof_serial = S.sieve_profile_read(ctx)
+    S.sieve_profile_enable(ctx, False)
+    S.sieve_sync(ctx)
     if pg:
         t = torch.tensor([ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -513,7 +522,14 @@ def main():
                 traffic["k_scatter"] = ts["dram_bytes"] / ts["units"] * (h_large / n_scatter)
     except Exception:
         pass
-    if t_tile >= t_scatter:
+    # the dominant kernel: the larger share of the step when the two run one after
+    # the other (the serialised step above)
+    st_tile, st_scatter = prof_serial["ms"][S.K_TILE], prof_serial["ms"][S.K_SCATTER]
+    kernels["serialised_step"] = {
+        "k_tile_ms": st_tile, "k_scatter_ms": st_scatter,
+        "k_tile_share": st_tile / (st_tile + st_scatter) if st_tile + st_scatter else None,
+        "k_scatter_share": st_scatter / (st_tile + st_scatter) if st_tile + st_scatter else None}
+    if st_tile >= st_scatter:
         ach = marks / t_tile / 1e9
         roof = {"kernel": "k_tile", "bound": "smem_atomic", "achieved": ach, "peak": r_atom / 1e9,
                 "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": traffic["k_tile"],

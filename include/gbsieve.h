@@ -199,9 +199,11 @@ sieve_status sieve_base_info(sieve_ctx *ctx, const uint32_t **dev_primes, uint64
 
 /*
  * Per-kernel timing of the device work of later calls, by CUDA events on the
- * call's stream (enable = 1 turns it on, 0 off).  sieve_profile_read waits for the
- * stream and returns, per kernel kind, the launches and the summed milliseconds
- * since the last read, plus work counters (hits emitted, bytes moved).
+ * stream each kernel runs on (enable = 1 turns it on, 0 off; 2 also runs the
+ * scatter and tile launches of a plan on one stream, one after the other, so that
+ * each kernel's time is its own rather than shared with the other overlapping
+ * it).  sieve_profile_read waits for the stream and returns, per kernel kind, the
+ * launches and the summed milliseconds since the last read, plus work counters.
  */
 typedef struct {
     uint64_t launches[8];    /* by kind, see SIEVE_K_* */
@@ -210,7 +212,7 @@ typedef struct {
     uint64_t bits;           /* table bits written */
     uint64_t large_hits;     /* bucket entries emitted (large-prime hits) */
     uint64_t medium_marks;   /* estimated in-tile marks by medium primes */
-    uint64_t prime_reads;    /* (prime, window) first-hit computations in the scatter */
+    uint64_t prime_reads;    /* (prime, scatter unit) visits in the scatter */
 } sieve_profile;
 #define SIEVE_K_TILE 0
 #define SIEVE_K_SCATTER 1

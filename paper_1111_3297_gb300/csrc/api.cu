@@ -608,7 +608,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
 {
     const uint32_t bt = P->tune.tile_log2;
     const uint32_t tgrid_max = (uint32_t)(c->nsm * tile_blocks_per_sm(bt));
-    cudaStream_t st = scr.s_tile, ss = scr.s_scat;
+    cudaStream_t st = scr.s_tile, ss = c->prof && c->prof_serial ? scr.s_tile : scr.s_scat;
     CK(cudaEventRecord(scr.ev_fork, ls));
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
     CK(cudaStreamWaitEvent(ss, scr.ev_fork, 0));
@@ -1196,6 +1196,7 @@ sieve_status sieve_profile_enable(sieve_ctx *c, int enable)
 {
     if (!c) return SIEVE_EINVAL;
     c->prof = enable != 0;
+    c->prof_serial = enable == 2;
     return SIEVE_OK;
 }
 

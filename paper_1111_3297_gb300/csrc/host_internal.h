@@ -133,6 +133,7 @@ struct sieve_ctx {
     std::map<std::string, std::unique_ptr<gbs::Plan>> plans;
     // profiling
     bool prof = false;
+    bool prof_serial = false;    // profiling with scatter and tile launches on one stream
     std::vector<gbs::ProfRec> prof_recs;
     sieve_profile prof_acc{};
     int sticky_err = 0;

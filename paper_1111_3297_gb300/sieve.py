@@ -229,8 +229,8 @@ def sieve_base_info(ctx):
     return p.value, c.value, lim.value
 
 
-def sieve_profile_enable(ctx, enable=True):
-    _check(lib().sieve_profile_enable(ctx.handle, 1 if enable else 0), "sieve_profile_enable")
+def sieve_profile_enable(ctx, enable=True, serial=False):
+    _check(lib().sieve_profile_enable(ctx.handle, (2 if serial else 1) if enable else 0), "sieve_profile_enable")
 
 
 def sieve_profile_read(ctx, stream=None):
