@@ -15,11 +15,12 @@
  * Layout: bit j is bit (j % 32) of 32-bit word j / 32 (least significant bit
  * first), words consecutive in memory.
  *
- * Errors: argument and allocation errors are returned at once.  Errors raised
- * on the device (a bucket overflow beyond the backstop, a bounded wait that ran
- * out) are recorded in the context and returned by the next call that waits
- * on the stream (sieve_count, sieve_sync, sieve_segments_host).  Functions are
- * not thread-safe on one context, except the server functions, which lock.
+ * Errors: argument and allocation errors are returned at once.  An error raised
+ * on the device (a bucket overflow beyond the backstop) is recorded in the
+ * context and returned by the next call that waits on the stream (sieve_count,
+ * sieve_sync, sieve_segments_host).  No kernel waits on another CTA or launch, so
+ * no device wait can hang.  Functions are not thread-safe on one context, except
+ * the server functions, which lock.
  */
 #ifndef GBSIEVE_H
 #define GBSIEVE_H
@@ -40,7 +41,7 @@ typedef enum {
     SIEVE_ERANGE = 2,    /* numbers beyond 2^64, or sqrt(v) beyond the context's base */
     SIEVE_ENOMEM = 3,    /* device or host allocation failed / over the memory budget */
     SIEVE_ECUDA = 4,     /* a CUDA runtime call failed */
-    SIEVE_ETIMEOUT = 5,  /* a bounded device or host wait ran out */
+    SIEVE_ETIMEOUT = 5,  /* a bounded wait ran out (reserved: no current call reports it) */
     SIEVE_EBUSY = 6,     /* server queue full / resource in use */
     SIEVE_EOVERFLOW = 7  /* large-prime bucket overflow beyond the backstop list */
 } sieve_status;
