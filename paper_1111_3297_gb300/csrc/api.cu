@@ -682,10 +682,21 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             const uint32_t run = (e.ntiles + tgrid - 1) / tgrid;
             if (((uint64_t)run << bt) < (1ull << 29) - 1) ta.run = run;
         }
+        // host output: the slot's previous copy must be done before the tiles overwrite it
+        if (P->host_out && ei >= 2) CK(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
         prof_mark(c, SIEVE_K_TILE, st, true);
         CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));
         prof_mark(c, SIEVE_K_TILE, st, false);
         CK(cudaEventRecord(scr.ev_tile[b], st));
+        if (P->host_out) {
+            CK(cudaEventRecord(c->ev_stage[b], st));
+            CK(cudaStreamWaitEvent(c->copy_stream, c->ev_stage[b], 0));
+            prof_mark(c, SIEVE_K_COPY, c->copy_stream, true);
+            CK(cudaMemcpyAsync(P->host_dst + P->ep_word0[ei], out + (size_t)b * P->slot_words,
+                               P->ep_words[ei] * 4, cudaMemcpyDeviceToHost, c->copy_stream));
+            prof_mark(c, SIEVE_K_COPY, c->copy_stream, false);
+            CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+        }
     }
     CK(cudaEventRecord(scr.ev_join, ss));
     CK(cudaStreamWaitEvent(st, scr.ev_join, 0));
@@ -1099,32 +1110,44 @@ sieve_status sieve_segments_host(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t 
     if (s) return s;
     CK(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
-    // windows of up to 2^31 bits, double-buffered on the device: sieve window k
-    // into stage k%2 on `stream`, copy it to the host on the copy stream
-    const uint64_t C = std::min<uint64_t>(nbits, 1ull << 31);
-    s = ensure((void **)&c->d_stage, &c->stage_bytes, 2 * (C / 8) + 64, nullptr);
-    if (s) return s;
-    uint32_t *stage[2] = {c->d_stage, c->d_stage + C / 32};
-    const sieve_tuning t = tuning_for(c, vlast, C);
-    const uint64_t nwin = (nbits + C - 1) / C;
-    for (uint64_t k = 0; k < nwin; ++k) {
-        const uint64_t wj = j0 + k * C, wn = std::min<uint64_t>(C, nbits - k * C);
-        const int b = (int)(k & 1);
-        if (k >= 2) CK(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
-        char key[160];
-        std::snprintf(key, sizeof key, "H/%llu/%llu/%p/", (unsigned long long)wj, (unsigned long long)wn,
-                      (void *)stage[b]);
-        std::vector<ReqSpec> reqs{{wj, wn, 0, 0}};
-        Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
-        s = run_plan(c, P, stage[b], nullptr, st, true);
-        if (s) return s;
-        CK(cudaEventRecord(c->ev_stage[b], st));
-        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_stage[b], 0));
-        prof_mark(c, SIEVE_K_COPY, c->copy_stream, true);
-        CK(cudaMemcpyAsync(host_bits + (k * C) / 32, stage[b], wn / 8, cudaMemcpyDeviceToHost, c->copy_stream));
-        prof_mark(c, SIEVE_K_COPY, c->copy_stream, false);
-        CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+    // One plan for the whole interval, epochs of at most 1024 tiles: each epoch's
+    // tiles go to ring slot (epoch mod 2) in device memory and are copied to the host
+    // on the copy stream while later epochs compute; a slot is reused once its copy
+    // is done.  Only the last epoch's copy is not hidden behind computation.
+    sieve_tuning t = tuning_for(c, vlast, nbits);
+    t.epoch_tiles = std::max(t.window_tiles, std::min<uint32_t>(t.epoch_tiles, 1024));
+    char key[96];
+    std::snprintf(key, sizeof key, "R/%llu/%llu/", (unsigned long long)j0, (unsigned long long)nbits);
+    std::vector<ReqSpec> reqs{{j0, nbits, 0, 0}};
+    Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
+    if (!P) return SIEVE_ENOMEM;
+    if (!P->host_out) {
+        // first use: output offsets into the ring (descriptors are not uploaded yet)
+        P->ep_word0.clear();
+        P->ep_words.clear();
+        uint64_t slot = 0;
+        for (const Plan::Epoch &e : P->epochs) {
+            uint64_t w = 0;
+            for (uint32_t k = 0; k < e.ntiles; ++k) w += P->tiles[e.tile0 + k].len / 32;
+            P->ep_word0.push_back(P->tiles[e.tile0].out_word);
+            P->ep_words.push_back(w);
+            slot = std::max<uint64_t>(slot, (w + 3) & ~3ull);  // 16-byte aligned slots
+        }
+        P->slot_words = slot;
+        for (size_t ei = 0; ei < P->epochs.size(); ++ei) {
+            const Plan::Epoch &e = P->epochs[ei];
+            for (uint32_t k = 0; k < e.ntiles; ++k) {
+                TileDesc &d = P->tiles[e.tile0 + k];
+                d.out_word = (ei & 1) * slot + (d.out_word - P->ep_word0[ei]);
+            }
+        }
+        P->host_out = true;
     }
+    s = ensure((void **)&c->d_stage, &c->stage_bytes, 2 * P->slot_words * 4 + 64, nullptr);
+    if (s) return s;
+    P->host_dst = host_bits;
+    s = run_plan(c, P, c->d_stage, nullptr, st, false);
+    if (s) return s;
     CK(cudaStreamSynchronize(c->copy_stream));
     return sieve_sync(c, stream);
 }

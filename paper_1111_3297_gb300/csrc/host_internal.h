@@ -48,6 +48,12 @@ struct Plan {
     uint32_t max_epoch_tiles = 0;
     uint64_t carry_entries = 0;  // carried-state slots the plan needs
     bool single_request = false; // all tiles belong to one request (tile runs may carry)
+    // host output: each epoch's tiles write into ring slot (epoch mod 2) of the output
+    // buffer, whose slot enqueue_plan copies to host_dst + ep_word0[e] after the epoch
+    bool host_out = false;
+    uint64_t slot_words = 0;
+    std::vector<uint64_t> ep_word0, ep_words;
+    uint32_t *host_dst = nullptr;
     bool run_scatter = false;    // single-request scatter: one state word per large prime
     uint32_t state_base = 0;     //   for the whole interval, primes from index state_base
     bool big_wheel = false;      // large primes use the mod-15015 wheel (else mod 15)
