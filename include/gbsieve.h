@@ -85,9 +85,10 @@ sieve_status sieve_segments_midpoint(sieve_ctx *ctx, uint32_t l, uint64_t mant, 
 
 /*
  * End-to-end form of sieve_segments: the table lands in caller-owned HOST memory
- * host_bits (n*2^(l-5) words; pinned memory copies fastest).  The context stages
- * the table on the device and copies it back window by window, overlapping the
- * copies with the sieving.  Waits until the table is in host_bits.
+ * host_bits (n*2^(l-5) words; pinned memory copies fastest).  The context sieves
+ * it in epochs of at most 2^30 bits into a two-slot device ring and copies each
+ * slot back while the next epochs are sieved (device memory: two epochs).  Waits
+ * until the table is in host_bits.
  */
 sieve_status sieve_segments_host(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
                                  uint32_t *host_bits, sieve_stream stream);
