@@ -218,14 +218,21 @@ def cpu_baseline(wl, f):
                       % (sample, n, l, dt, cores)}
 
 
-def kernel_code_hash(path):
-    """SHA-256 (16 hex digits) of a CUDA source with comments and blank lines removed:
-    the key under which profiles/traffic.json stores counters of that code."""
+KERNEL_SOURCES = ("kernels.cu", "sieve_internal.cuh")  # everything compiled into the kernels
+
+
+def kernel_code_hash(csrc):
+    """SHA-256 (16 hex digits) of the kernels' CUDA sources with comments and blank
+    lines removed: the key under which profiles/traffic.json stores counters of that
+    code."""
     import hashlib
     import re
-    src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
-    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.split("\n")]
-    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(csrc, name)).read(), flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.split("\n")]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
+    return h.hexdigest()[:16]
 
 
 def measure_sweep(S, ctx, hbm_peak, r_atom):
@@ -508,13 +515,13 @@ def main():
     }
     # DRAM traffic per launch from the committed ncu capture of the same kernel on a
     # smaller slice of the same workload, scaled by the kernel's units per launch;
-    # null when the code of kernels.cu changed since the capture
+    # null when the kernels' code (kernels.cu, sieve_internal.cuh) changed since the capture
     traffic = {"k_tile": None, "k_scatter": None}
     try:
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ksha = kernel_code_hash(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc", "kernels.cu"))
+        ksha = kernel_code_hash(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc"))
         key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload)
-        if key and tj.get("kernels_cu_code_sha256_16") == ksha and key in tj:
+        if key and tj.get("kernel_code_sha256_16") == ksha and key in tj:
             tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
             if n_tile:
                 traffic["k_tile"] = tt["dram_bytes"] / tt["units"] * (N / n_tile)
