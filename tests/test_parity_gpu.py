@@ -263,3 +263,15 @@ def test_segments_larger_than_a_tile_equal_small_segments(ctx):
         j = rng.below(2 << 30)
         bit = (int(big[j // 32].item()) >> (j % 32)) & 1
         assert bit == (0 if oracle.is_prime_mr(2 * (J0 + j) + 1) else 1), j
+
+
+def test_host_output_small_and_repeated(ctx):
+    """Host output for tables of one word to one tile, twice each: the second call
+    reuses the cached plan and must write the new host buffer."""
+    for (l, f, n) in [(5, 3, 1), (5, 3, 7), (12, 1000, 3), (20, 2 ** 30, 1)]:
+        want = oracle.sieve(l, f, n)
+        for _ in range(2):
+            host = torch.full(((n << l) // 32,), -1, dtype=torch.int32).pin_memory()
+            S.sieve_segments_host(ctx, l, f, n, host)
+            got = host.numpy().view(np.uint32)
+            assert first_diff(got, want) is None, (l, f, n, first_diff(got, want))
