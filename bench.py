@@ -161,9 +161,12 @@ def step_roofline(N, marks, h_large, visits, t_step, hbm_peak, r_atom):
 
 
 def base_primes_upto(x):
+    """Odd primes <= x (index i stands for 2i+1)."""
     import numpy as np
     x = int(x)
-    s = np.ones(x // 2 + 1, dtype=bool)
+    if x < 3:
+        return np.zeros(0, dtype=np.int64)
+    s = np.ones((x - 1) // 2 + 1, dtype=bool)
     s[0] = False
     for i in range(1, (int(x ** 0.5) + 1) // 2 + 1):
         if s[i]:
