@@ -17,6 +17,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1e12..1e18 midpoint sweep")
+    ap.add_argument("--clocks-csv", default="",
+                    help="where to keep the nvidia-smi samples of the timed region (default: a temp file)")
     return ap.parse_args()
 
 
@@ -63,14 +66,14 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device):
+    def __init__(self, device, path=""):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.path = path or os.path.join(tempfile.gettempdir(), "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -428,7 +431,7 @@ def main():
     # ---- timed region: K steps, per-kernel CUDA events inside the library ----
     S.sieve_profile_enable(ctx, True)
     S.sieve_profile_read(ctx)  # reset
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_csv)
     clocks.start()
     if pg:
         pg.barrier()
