@@ -54,7 +54,8 @@ const char *sieve_strerror(sieve_status s);
  * largest number is <= max_v.  Builds the base of Sec. 1.4 (Definition "base":
  * the odd primes p <= sqrt(max_v)) on the device and keeps it resident with one
  * 64-bit reduction constant per prime.  mem_budget bounds the device memory the
- * context uses for large-prime buckets (0 = 16 GiB, split into two pools).
+ * context uses for large-prime buckets (0 = 16 GiB; otherwise at least 64 MiB,
+ * else SIEVE_EINVAL; split into two pools of mem_budget / 8 slots).
  * Waits for the device.
  * On success *ctx owns all its device memory until sieve_destroy.
  */
@@ -231,6 +232,70 @@ sieve_status sieve_profile_read(sieve_ctx *ctx, sieve_profile *out, sieve_stream
  * Waits for the device.
  */
 sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s);
+
+/*
+ * Planner inspection on the host, without a device.  Builds the plan sieve_batch
+ * builds for the requests `reqs` (rules as for sieve_batch): the work
+ * decomposition of Sec. 1.3 (segments = tiles) and Sec. 2.2 (large primes in
+ * per-tile buckets), and reports its shape.  A single request with tuning t is
+ * the plan sieve_segments runs for that interval with that tuning.
+ *   host_primes  the base: all odd primes 3 <= p <= isqrt(max_v), ascending (host
+ *                memory, nprimes of them; the caller vouches for completeness,
+ *                only order, oddness and the bound are checked);
+ *   nsm          SMs to plan chunks for (1..1024);
+ *   t            tuning (ranges as for sieve_set_tuning); NULL = the default of
+ *                the largest request's class;
+ *   pool_entries bucket slots per epoch (>= 4096, at most 2^32 - 2^22).
+ *                sieve_init's contexts have mem_budget / 8 of them.
+ * *info receives the counts.  tiles / groups / chunks may each be NULL; otherwise
+ * they receive the first max_* records (the counts in *info say how many exist).
+ * Records hold base-prime indices (0 = the prime 3) and bit indices as in sieve_req.
+ * Caller owns every buffer; nothing is retained.  Errors: SIEVE_EINVAL (null info,
+ * bad primes, tuning or sizes; request rules of sieve_batch), SIEVE_ERANGE (a
+ * request beyond max_v or 2^64).
+ */
+typedef struct {
+    uint64_t ntiles, ngroups, nepochs, nchunks, nunits;
+    uint64_t bits;             /* table bits of all tiles */
+    uint64_t pool_entries;     /* bucket slots of the largest epoch */
+    uint64_t carry_entries;    /* carried large-prime state slots */
+    uint32_t max_epoch_tiles;
+    uint32_t big_wheel;        /* 1: large primes on the mod-15015 wheel, 0: mod 15 */
+    uint32_t run_scatter;      /* 1: one state word per large prime for the interval */
+    uint32_t carried_groups;   /* groups whose large-prime state comes from the previous one */
+    uint32_t med_lo, blk_hi, coop_hi, large_lo; /* base-index bounds of the striking phases */
+    double expected_large_hits;
+} sieve_plan_info;
+
+typedef struct {
+    uint64_t j0;          /* first bit index */
+    uint64_t out_word;    /* output word offset */
+    uint64_t bkt_off;     /* bucket offset in its epoch's pool */
+    uint32_t len;         /* bits */
+    uint32_t req;         /* request index */
+    uint32_t epoch;
+    uint32_t group;       /* scatter group, UINT32_MAX when the tile has no large primes */
+    uint32_t bkt_cap;     /* bucket slots */
+    uint32_t med_hi;      /* medium primes are base indices [med_lo, med_hi) */
+} sieve_plan_tile;
+
+typedef struct {
+    uint32_t epoch, tile0, ntiles;  /* tiles [tile0, tile0 + ntiles), plan-wide indices */
+    uint32_t nunits;                /* scatter units (runs of one request) */
+    uint32_t p_lo, p_hi;            /* large primes, base indices [p_lo, p_hi) */
+    uint32_t carry_in, carry_out;
+} sieve_plan_group;
+
+typedef struct {
+    uint32_t epoch, p_lo, p_hi;     /* one scatter CTA: base indices [p_lo, p_hi) */
+} sieve_plan_chunk;
+
+sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, uint64_t max_v, uint32_t nsm,
+                                 const sieve_req *reqs, uint32_t count, const sieve_tuning *t,
+                                 uint64_t pool_entries, sieve_plan_info *info,
+                                 sieve_plan_tile *tiles, uint64_t max_tiles,
+                                 sieve_plan_group *groups, uint64_t max_groups,
+                                 sieve_plan_chunk *chunks, uint64_t max_chunks);
 
 /*
  * Serving: a request loop with continuous batching.  Requests are submitted

@@ -156,6 +156,19 @@ double inv_sum(const sieve_ctx *c, uint32_t a, uint32_t b)
     return c->h_inv_prefix[std::min<size_t>(bb, c->h_inv_prefix.size() - 1)] - c->h_inv_prefix[ba];
 }
 
+// the 1/p prefix table of the host copy of the base (chunk and bucket sizing)
+void host_prime_tables(sieve_ctx *c)
+{
+    c->nprimes = c->h_primes.size();
+    c->h_inv_prefix.assign(c->nprimes / kInvBlock + 2, 0.0);
+    double acc = 0;
+    for (uint64_t i = 0; i < c->nprimes; ++i) {
+        if (i % kInvBlock == 0) c->h_inv_prefix[i / kInvBlock] = acc;
+        acc += 1.0 / c->h_primes[i];
+    }
+    for (uint64_t k = (c->nprimes + kInvBlock - 1) / kInvBlock; k < c->h_inv_prefix.size(); ++k) c->h_inv_prefix[k] = acc;
+}
+
 uint32_t tune_class(uint64_t vlast)
 {
     const int lg = 63 - __builtin_clzll(vlast | 1);
@@ -452,7 +465,9 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
             if (large) {
                 const double e = (double)d.len * density * ri.inv;
                 cap = (uint32_t)std::ceil(1.05 * e + 8.0 * std::sqrt(e) + 64.0) + ri.nsmall_large;
-                cap = (cap + 3) & ~3u;
+                // never more than the pool holds (pools hold >= 4096 slots): hits past a
+                // bucket's capacity go to the backstop list, or raise the overflow error
+                cap = (uint32_t)std::min<uint64_t>((cap + 3) & ~3u, pool_cap & ~3ull);
             }
             // a new scatter group when the current one is full or this tile has no
             // large primes; a new epoch when the tile count or the pool is exhausted
@@ -501,7 +516,6 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     }
     close_group();
     close_epoch();
-    if (P->pool_entries > pool_cap) P->pool_entries = pool_cap;
     for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
     make_chunks(c, P.get());
     P->single_request = reqs.size() == 1;
@@ -872,13 +886,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
     c->h_primes.resize(c->nprimes);
     if (c->nprimes) CK(cudaMemcpyAsync(c->h_primes.data(), c->d_primes, c->nprimes * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    c->h_inv_prefix.assign(c->nprimes / kInvBlock + 2, 0.0);
-    double acc = 0;
-    for (uint64_t i = 0; i < c->nprimes; ++i) {
-        if (i % kInvBlock == 0) c->h_inv_prefix[i / kInvBlock] = acc;
-        acc += 1.0 / c->h_primes[i];
-    }
-    for (uint64_t k = (c->nprimes + kInvBlock - 1) / kInvBlock; k < c->h_inv_prefix.size(); ++k) c->h_inv_prefix[k] = acc;
+    host_prime_tables(c);
     return SIEVE_OK;
 }
 
@@ -886,6 +894,7 @@ sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_
 {
     if (!out) return SIEVE_EINVAL;
     *out = nullptr;
+    if (mem_budget && mem_budget < ((size_t)64 << 20)) return SIEVE_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -1189,6 +1198,85 @@ sieve_status sieve_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t count, ui
     Plan *P = cached_plan(c, std::string(key) + tune_key(t), rs, t);
     (void)total;
     return run_plan_n(c, P, dev_arena, (unsigned long long *)dev_counts, count, (cudaStream_t)stream, true);
+}
+
+sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, uint64_t max_v, uint32_t nsm,
+                                 const sieve_req *reqs, uint32_t count, const sieve_tuning *tp,
+                                 uint64_t pool_entries, sieve_plan_info *info, sieve_plan_tile *tiles,
+                                 uint64_t max_tiles, sieve_plan_group *groups, uint64_t max_groups,
+                                 sieve_plan_chunk *chunks, uint64_t max_chunks)
+{
+    if (!info || (nprimes && !host_primes) || (count && !reqs) || nsm == 0 || nsm > 1024 ||
+        pool_entries < 4096 || pool_entries > (1ull << 32) - (1ull << 22) || nprimes >= (1ull << 32) - kPrimePad)
+        return SIEVE_EINVAL;
+    if (tp && !tuning_valid(*tp)) return SIEVE_EINVAL;
+    *info = sieve_plan_info{};
+    // a host-only context: the base and the tables the planner reads, no device state
+    sieve_ctx c{};
+    c.nsm = (int)nsm;
+    c.max_v = max_v;
+    c.base_limit = std::min<uint64_t>(isqrt_u64(max_v), 0xFFFFFFFFull);
+    for (uint64_t i = 0; i < nprimes; ++i)
+        if (host_primes[i] < 3 || !(host_primes[i] & 1) || (i && host_primes[i] <= host_primes[i - 1]) ||
+            host_primes[i] > c.base_limit)
+            return SIEVE_EINVAL;
+    if (count == 0) return SIEVE_OK;
+    c.h_primes.assign(host_primes, host_primes + nprimes);
+    host_prime_tables(&c);
+    build_presieve(c.pre);
+    // requests as sieve_batch takes them: checked, then largest magnitude first
+    std::vector<ReqSpec> rs(count);
+    std::vector<uint64_t> vl(count);
+    uint64_t vmax = 0;
+    for (uint32_t r = 0; r < count; ++r) {
+        sieve_status s = check_range(&c, reqs[r].j0, reqs[r].nbits, &vl[r]);
+        if (s) return s;
+        rs[r] = ReqSpec{reqs[r].j0, reqs[r].nbits, reqs[r].out_word_off, r};
+        vmax = std::max(vmax, vl[r]);
+    }
+    std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
+    const sieve_tuning t = tp ? *tp : default_tuning(tune_class(vmax));
+    std::unique_ptr<Plan> P = build_plan(&c, rs, t, pool_entries);
+
+    info->ntiles = P->tiles.size();
+    info->ngroups = P->groups.size();
+    info->nepochs = P->epochs.size();
+    info->nchunks = P->chunks.size();
+    info->nunits = P->sus.size();
+    info->bits = P->bits;
+    info->pool_entries = P->pool_entries;
+    info->carry_entries = P->carry_entries;
+    info->max_epoch_tiles = P->max_epoch_tiles;
+    info->big_wheel = P->big_wheel;
+    info->run_scatter = P->run_scatter;
+    for (const GroupDesc &G : P->groups) info->carried_groups += G.carry_in;
+    info->med_lo = P->med_lo;
+    info->blk_hi = P->blk_hi;
+    info->coop_hi = P->coop_hi;
+    info->large_lo = std::max(P->med_lo, prime_count_le(&c, t.medium_max));
+    info->expected_large_hits = P->exp_large_hits;
+
+    std::vector<uint32_t> tile_group(P->tiles.size(), 0xFFFFFFFFu), tile_epoch(P->tiles.size(), 0);
+    for (uint32_t e = 0; e < P->epochs.size(); ++e) {
+        const Plan::Epoch &E = P->epochs[e];
+        for (uint32_t k = 0; k < E.ntiles; ++k) tile_epoch[E.tile0 + k] = e;
+        for (uint32_t g = 0; g < E.ng; ++g) {
+            const GroupDesc &G = P->groups[E.g0 + g];
+            for (uint32_t k = 0; k < G.ntiles; ++k) tile_group[E.tile0 + G.tile0 + k] = E.g0 + g;
+            if (groups && E.g0 + g < max_groups)
+                groups[E.g0 + g] = sieve_plan_group{e, E.tile0 + G.tile0, G.ntiles, G.nsu, G.p_lo, G.p_hi,
+                                                    G.carry_in, G.carry_out};
+        }
+        for (uint32_t k = 0; k < E.nc; ++k)
+            if (chunks && E.c0 + k < max_chunks)
+                chunks[E.c0 + k] = sieve_plan_chunk{e, P->chunks[E.c0 + k].p_lo, P->chunks[E.c0 + k].p_hi};
+    }
+    for (uint64_t i = 0; tiles && i < std::min<uint64_t>(max_tiles, P->tiles.size()); ++i) {
+        const TileDesc &d = P->tiles[i];
+        tiles[i] = sieve_plan_tile{d.J, d.out_word, d.bkt_off, d.len, d.req, tile_epoch[i], tile_group[i],
+                                   d.bkt_cap, d.med_hi};
+    }
+    return SIEVE_OK;
 }
 
 sieve_status sieve_get_tuning(sieve_ctx *c, uint32_t cls, sieve_tuning *out)

@@ -150,6 +150,7 @@ extern char g_last_cuda_error[512];
 uint64_t isqrt_u64(uint64_t x);
 uint32_t prime_count_le(const sieve_ctx *c, uint64_t x);
 double inv_sum(const sieve_ctx *c, uint32_t a, uint32_t b);
+void host_prime_tables(sieve_ctx *c);
 uint32_t tune_class(uint64_t vlast);
 sieve_tuning default_tuning(uint32_t cls);
 bool tuning_valid(const sieve_tuning &t);

@@ -44,6 +44,31 @@ class Profile(ctypes.Structure):
                 ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64)]
 
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("ntiles", _u64), ("ngroups", _u64), ("nepochs", _u64), ("nchunks", _u64), ("nunits", _u64),
+                ("bits", _u64), ("pool_entries", _u64), ("carry_entries", _u64), ("max_epoch_tiles", _u32),
+                ("big_wheel", _u32), ("run_scatter", _u32), ("carried_groups", _u32), ("med_lo", _u32),
+                ("blk_hi", _u32), ("coop_hi", _u32), ("large_lo", _u32), ("expected_large_hits", _dbl)]
+
+
+class PlanTile(ctypes.Structure):
+    _fields_ = [("j0", _u64), ("out_word", _u64), ("bkt_off", _u64), ("len", _u32), ("req", _u32),
+                ("epoch", _u32), ("group", _u32), ("bkt_cap", _u32), ("med_hi", _u32)]
+
+
+class PlanGroup(ctypes.Structure):
+    _fields_ = [("epoch", _u32), ("tile0", _u32), ("ntiles", _u32), ("nunits", _u32), ("p_lo", _u32),
+                ("p_hi", _u32), ("carry_in", _u32), ("carry_out", _u32)]
+
+
+class PlanChunk(ctypes.Structure):
+    _fields_ = [("epoch", _u32), ("p_lo", _u32), ("p_hi", _u32)]
+
+
+def _rec(x):
+    return {k: getattr(x, k) for k, _ in x._fields_}
+
+
 class Result(ctypes.Structure):
     _fields_ = [("id", _u64), ("j0", _u64), ("nbits", _u64), ("composites", _u64),
                 ("dev_bits", _vp), ("t_submit", _dbl), ("t_admit", _dbl), ("t_done", _dbl),
@@ -77,6 +102,10 @@ def lib():
             "sieve_profile_enable": (_i32, [_vp, _i32]),
             "sieve_profile_read": (_i32, [_vp, ctypes.POINTER(Profile), _vp]),
             "sieve_probe_smem_atomics": (_i32, [_i32, ctypes.POINTER(_dbl)]),
+            "sieve_plan_describe": (_i32, [_vp, _u64, _u64, _u32, ctypes.POINTER(Req), _u32,
+                                           ctypes.POINTER(Tuning), _u64, ctypes.POINTER(PlanInfo),
+                                           ctypes.POINTER(PlanTile), _u64, ctypes.POINTER(PlanGroup), _u64,
+                                           ctypes.POINTER(PlanChunk), _u64]),
             "sieve_server_create": (_i32, [_vp, ctypes.c_size_t, _u32, ctypes.POINTER(_vp)]),
             "sieve_server_submit": (_i32, [_vp, _u64, _u64, ctypes.POINTER(_u64)]),
             "sieve_server_poll": (_i32, [_vp, ctypes.POINTER(Result), _u32, ctypes.POINTER(_u32), _u32]),
@@ -244,6 +273,38 @@ def sieve_probe_smem_atomics(device=0):
     r = _dbl()
     _check(lib().sieve_probe_smem_atomics(device, ctypes.byref(r)), "sieve_probe_smem_atomics")
     return r.value
+
+
+def sieve_plan_describe(primes, max_v, nsm, reqs, tuning=None, pool_entries=1 << 31, records=True):
+    """The plan sieve_batch builds for reqs ((j0, nbits, out_word_off) each), on the host
+    without a device, from the base `primes` (all odd primes <= isqrt(max_v), ascending).
+    tuning: dict of sieve_tuning fields, or None for the class default.  Returns
+    {"info": {...}} plus, with records, lists "tiles", "groups" and "chunks" of dicts."""
+    import numpy as np
+    pr = np.ascontiguousarray(primes, dtype=np.uint32)
+    arr = _reqs(reqs)
+    tp = None
+    if tuning is not None:
+        t = Tuning(**tuning)
+        tp = ctypes.byref(t)
+    info = PlanInfo()
+    L = lib()
+
+    def call(tiles, nt, groups, ng, chunks, nc):
+        _check(L.sieve_plan_describe(pr.ctypes.data_as(_vp), len(pr), max_v, nsm, arr, len(reqs), tp,
+                                     pool_entries, ctypes.byref(info), tiles, nt, groups, ng, chunks, nc),
+               "sieve_plan_describe")
+    call(None, 0, None, 0, None, 0)
+    out = {"info": _rec(info)}
+    if records:
+        tiles = (PlanTile * info.ntiles)()
+        groups = (PlanGroup * info.ngroups)()
+        chunks = (PlanChunk * info.nchunks)()
+        call(tiles, info.ntiles, groups, info.ngroups, chunks, info.nchunks)
+        out["tiles"] = [_rec(x) for x in tiles]
+        out["groups"] = [_rec(x) for x in groups]
+        out["chunks"] = [_rec(x) for x in chunks]
+    return out
 
 
 class Server:

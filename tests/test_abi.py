@@ -58,6 +58,14 @@ def test_host_only_entry_points_work_without_a_gpu(lib):
     assert lib.sieve_f_from_midpoint(20, 1, 5, 19, ctypes.byref(f)) == 2  # 5e19 > 2^64
 
 
+def test_init_rejects_a_bucket_budget_below_64_mib(lib):
+    # checked before any device call, so it answers without a GPU
+    h = ctypes.c_void_p()
+    lib.sieve_init.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t]
+    assert lib.sieve_init(ctypes.byref(h), 0, 1 << 40, (64 << 20) - 1) == 1
+    assert h.value is None
+
+
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     from paper_1111_3297_gb300 import sieve as S
     monkeypatch.setattr(S, "_lib", None)

@@ -194,3 +194,46 @@ def test_batch_with_epochs_longer_than_2p32_bits(ctx):
     finally:
         for k in range(4):
             S.sieve_set_tuning(ctx, k, **saved[k])
+
+
+def test_server_lane_pool_smaller_than_one_tile_bucket(ctx):
+    """Server lanes of a 256 MiB cap shared by 16 hold 2^19 bucket slots per pool.  With
+    every prime above the pre-sieve taken as large (medium_max 0), one 2^20-bit tile
+    near 2^62 expects about 7.4e5 large-prime hits, more than the pool, so the planner
+    clamps its bucket to the pool and the rest goes through the backstop list.  The
+    served table must equal the plain call (whose small tiles need no clamp) bit for
+    bit, and Miller-Rabin on sampled bits."""
+    import oracle
+    saved = [S.sieve_get_tuning(ctx, k) for k in range(4)]
+    srv = None
+    try:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, tile_log2=20, presieve_groups=2, coop_max=4096, medium_max=0,
+                               window_tiles=1024, epoch_tiles=4096)
+        nb = 1 << 21
+        j0 = (1 << 61) - (1 << 22)
+        srv = S.Server(ctx, mem_cap=256 << 20, max_inflight=16)
+        rid = srv.submit(j0, nb)
+        got, deadline = [], time.time() + 120
+        while not got and time.time() < deadline:
+            got = srv.poll(8, timeout_ms=1000)
+        assert len(got) == 1 and got[0]["id"] == rid and got[0]["status"] == 0
+        served = torch.as_tensor(_DevArray(got[0]["dev_bits"], nb // 32), device="cuda").clone()
+        composites = got[0]["composites"]
+        srv.release(rid)
+        plain = torch.empty(nb // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments(ctx, 5, j0 // 32, nb // 32, plain)
+        S.sieve_sync(ctx)
+        assert torch.equal(served, plain)
+        assert composites == S.sieve_count(ctx, plain, nb)
+        rng = workloads.SplitMix64(62)
+        host = served.cpu().numpy().view(np.uint32)
+        for _ in range(300):
+            j = rng.below(nb)
+            bit = (int(host[j // 32]) >> (j % 32)) & 1
+            assert bit == (0 if oracle.is_prime_mr(2 * (j0 + j) + 1) else 1), j
+    finally:
+        if srv is not None:
+            srv.close()
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **saved[k])
