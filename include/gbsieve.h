@@ -18,7 +18,9 @@
  * Errors: argument and allocation errors are returned at once.  An error raised
  * on the device (a bucket overflow beyond the backstop) is recorded in the
  * context and returned by the next call that waits on the stream (sieve_count,
- * sieve_sync, sieve_segments_host).  No kernel waits on another CTA or launch, so
+ * sieve_sync, sieve_segments_host).  A call whose work would exceed 2^31 on-chip
+ * tiles returns SIEVE_ERANGE; host allocation failures return SIEVE_ENOMEM (no C++
+ * exception crosses this interface).  No kernel waits on another CTA or launch, so
  * no device wait can hang.  Functions are not thread-safe on one context, except
  * the server functions, which lock.
  */

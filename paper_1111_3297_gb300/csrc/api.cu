@@ -358,10 +358,16 @@ static void make_chunks(sieve_ctx *c, Plan *P)
 
 std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tuning t, uint64_t pool_cap_in)
 {
-    std::unique_ptr<Plan> P(new Plan());
-    P->tune = t;
     const uint32_t bt = t.tile_log2;
     const uint64_t B = 1ull << bt;
+    {
+        // tiles, groups and epochs are addressed with 32-bit indices
+        uint64_t ntiles = 0;
+        for (const ReqSpec &q : reqs) ntiles += (q.nbits + B - 1) / B;
+        if (ntiles >= (1ull << 31)) return nullptr;
+    }
+    std::unique_ptr<Plan> P(new Plan());
+    P->tune = t;
     P->ps.ngroups = t.presieve_groups;
     for (int g = 0; g < kMaxPresieveGroups; ++g) {
         P->ps.modulus[g] = c->pre.modulus[g];
@@ -891,7 +897,7 @@ static sieve_status build_base(sieve_ctx *c, cudaStream_t st)
 }
 
 sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_budget)
-{
+try {
     if (!out) return SIEVE_EINVAL;
     *out = nullptr;
     if (mem_budget && mem_budget < ((size_t)64 << 20)) return SIEVE_EINVAL;
@@ -947,6 +953,8 @@ sieve_status sieve_init(sieve_ctx **out, int device, uint64_t max_v, size_t mem_
     }
     *out = c.release();
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 void sieve_destroy(sieve_ctx *c)
@@ -1020,6 +1028,7 @@ Plan *cached_plan(sieve_ctx *c, const std::string &key, const std::vector<ReqSpe
         c->plans.clear();
     }
     std::unique_ptr<Plan> P = build_plan(c, reqs, t);
+    if (!P) return nullptr;
     Plan *raw = P.get();
     c->plans[key] = std::move(P);
     return raw;
@@ -1029,7 +1038,7 @@ Plan *cached_plan(sieve_ctx *c, const std::string &key, const std::vector<ReqSpe
 
 sieve_status sieve_segments(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, uint32_t *dev_bits,
                             sieve_stream stream)
-{
+try {
     if (!c || !dev_bits || l < 5 || l > 40 || n == 0 || ((uintptr_t)dev_bits & 3)) return SIEVE_EINVAL;
     if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
     const uint64_t j0 = f << l, nbits = n << l;
@@ -1043,7 +1052,10 @@ sieve_status sieve_segments(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, ui
                   (void *)dev_bits);
     std::vector<ReqSpec> reqs{{j0, nbits, 0, 0}};
     Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
+    if (!P) return SIEVE_ERANGE;
     return run_plan(c, P, dev_bits, nullptr, (cudaStream_t)stream, true);
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_f_from_midpoint(uint32_t l, uint64_t n, uint64_t mant, uint32_t exp10, uint64_t *f_out)
@@ -1110,7 +1122,7 @@ sieve_status sieve_count(sieve_ctx *c, const uint32_t *dev_bits, uint64_t nbits,
 
 sieve_status sieve_segments_host(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, uint32_t *host_bits,
                                  sieve_stream stream)
-{
+try {
     if (!c || !host_bits || l < 5 || l > 40 || n == 0) return SIEVE_EINVAL;
     if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
     const uint64_t j0 = f << l, nbits = n << l;
@@ -1129,7 +1141,7 @@ sieve_status sieve_segments_host(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t 
     std::snprintf(key, sizeof key, "R/%llu/%llu/", (unsigned long long)j0, (unsigned long long)nbits);
     std::vector<ReqSpec> reqs{{j0, nbits, 0, 0}};
     Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
-    if (!P) return SIEVE_ENOMEM;
+    if (!P) return SIEVE_ERANGE;
     if (!P->host_out) {
         // first use: output offsets into the ring (descriptors are not uploaded yet)
         P->ep_word0.clear();
@@ -1159,11 +1171,13 @@ sieve_status sieve_segments_host(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t 
     if (s) return s;
     CK(cudaStreamSynchronize(c->copy_stream));
     return sieve_sync(c, stream);
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t count, uint32_t *dev_arena,
                          uint64_t *dev_counts, sieve_stream stream)
-{
+try {
     if (!c || (count && (!reqs || !dev_arena || !dev_counts)) || ((uintptr_t)dev_arena & 3)) return SIEVE_EINVAL;
     if (count == 0) return SIEVE_OK;
     CK(cudaSetDevice(c->device));
@@ -1196,8 +1210,11 @@ sieve_status sieve_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t count, ui
     std::snprintf(key, sizeof key, "B/%u/%016llx/%p/%p/", count, (unsigned long long)h, (void *)dev_arena,
                   (void *)dev_counts);
     Plan *P = cached_plan(c, std::string(key) + tune_key(t), rs, t);
+    if (!P) return SIEVE_ERANGE;
     (void)total;
     return run_plan_n(c, P, dev_arena, (unsigned long long *)dev_counts, count, (cudaStream_t)stream, true);
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, uint64_t max_v, uint32_t nsm,
@@ -1205,7 +1222,7 @@ sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, 
                                  uint64_t pool_entries, sieve_plan_info *info, sieve_plan_tile *tiles,
                                  uint64_t max_tiles, sieve_plan_group *groups, uint64_t max_groups,
                                  sieve_plan_chunk *chunks, uint64_t max_chunks)
-{
+try {
     if (!info || (nprimes && !host_primes) || (count && !reqs) || nsm == 0 || nsm > 1024 ||
         pool_entries < 4096 || pool_entries > (1ull << 32) - (1ull << 22) || nprimes >= (1ull << 32) - kPrimePad)
         return SIEVE_EINVAL;
@@ -1237,6 +1254,7 @@ sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, 
     std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
     const sieve_tuning t = tp ? *tp : default_tuning(tune_class(vmax));
     std::unique_ptr<Plan> P = build_plan(&c, rs, t, pool_entries);
+    if (!P) return SIEVE_ERANGE;
 
     info->ntiles = P->tiles.size();
     info->ngroups = P->groups.size();
@@ -1277,6 +1295,8 @@ sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, 
                                    d.bkt_cap, d.med_hi};
     }
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_get_tuning(sieve_ctx *c, uint32_t cls, sieve_tuning *out)
@@ -1312,7 +1332,7 @@ sieve_status sieve_profile_enable(sieve_ctx *c, int enable)
 }
 
 sieve_status sieve_profile_read(sieve_ctx *c, sieve_profile *out, sieve_stream stream)
-{
+try {
     if (!c || !out) return SIEVE_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1335,6 +1355,8 @@ sieve_status sieve_profile_read(sieve_ctx *c, sieve_profile *out, sieve_stream s
     c->prof_acc = sieve_profile{};
     CK(cudaMemset(c->scr.d_acc + 1, 0, 8));
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s)

@@ -119,7 +119,7 @@ struct sieve_server {
 };
 
 bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
-{
+try {
     std::vector<ReqSpec> rs(batch.size());
     std::vector<uint64_t> vl(batch.size());
     uint64_t vmax = 0;
@@ -132,7 +132,8 @@ bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
     const sieve_tuning t = c->batch_tune.tile_log2 ? c->batch_tune : c->tune[tune_class(vmax)];
     L.plan = build_plan(c, rs, t, L.scr.pool_entries);
     Plan *P = L.plan.get();
-    sieve_status s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles, P->carry_entries);
+    sieve_status s = P ? SIEVE_OK : SIEVE_ERANGE;
+    if (!s) s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles, P->carry_entries);
     if (!s) s = upload_plan(c, P, L.st);
     if (!s) s = enqueue_plan(c, L.scr, P, d_arena, L.d_counts, (uint32_t)batch.size(), L.st);
     if (!s && cudaMemcpyAsync(L.h_counts, L.d_counts, batch.size() * 8, cudaMemcpyDeviceToHost, L.st) != cudaSuccess)
@@ -150,6 +151,16 @@ bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
         return false;
     }
     return true;
+} catch (...) {
+    // host memory ran out while planning or enqueueing (this runs on the server's
+    // thread, which an escaping exception would end): wait for whatever was
+    // enqueued, then finish the batch with the error
+    cudaStreamSynchronize(L.st);
+    L.reqs = batch;
+    L.busy = true;
+    for (Req *r : L.reqs) r->status = SIEVE_ENOMEM;
+    *L.h_err = 0;
+    return false;
 }
 
 void sieve_server::complete(Lane &L)
@@ -225,7 +236,7 @@ void sieve_server::loop()
 }
 
 sieve_status sieve_server_create(sieve_ctx *c, size_t mem_cap, uint32_t max_inflight, sieve_server **out)
-{
+try {
     if (!c || !out || max_inflight == 0 || max_inflight > 16 || mem_cap < ((size_t)256 << 20)) return SIEVE_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) return SIEVE_ECUDA;
     std::unique_ptr<sieve_server> S(new sieve_server());
@@ -260,10 +271,12 @@ sieve_status sieve_server_create(sieve_ctx *c, size_t mem_cap, uint32_t max_infl
     raw->th = std::thread([raw] { raw->loop(); });
     *out = raw;
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_server_submit(sieve_server *S, uint64_t j0, uint64_t nbits, uint64_t *id)
-{
+try {
     if (!S || !id) return SIEVE_EINVAL;
     uint64_t vlast;
     sieve_status s = check_range(S->c, j0, nbits, &vlast);
@@ -287,10 +300,12 @@ sieve_status sieve_server_submit(sieve_server *S, uint64_t j0, uint64_t nbits, u
     *id = r->id;
     S->cv_work.notify_one();
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_server_poll(sieve_server *S, sieve_result *out, uint32_t max, uint32_t *n, uint32_t timeout_ms)
-{
+try {
     if (!S || !n || (max && !out)) return SIEVE_EINVAL;
     *n = 0;
     std::unique_lock<std::mutex> g(S->mu);
@@ -311,10 +326,12 @@ sieve_status sieve_server_poll(sieve_server *S, sieve_result *out, uint32_t max,
         o.status = r->status;
     }
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_server_release(sieve_server *S, uint64_t id)
-{
+try {
     if (!S) return SIEVE_EINVAL;
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->live.find(id);
@@ -324,6 +341,8 @@ sieve_status sieve_server_release(sieve_server *S, uint64_t id)
     S->live.erase(it);
     S->cv_work.notify_one();
     return SIEVE_OK;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 double sieve_server_now(sieve_server *S) { return S ? S->now() : 0.0; }

@@ -29,7 +29,7 @@ double time_tuning(sieve_ctx *c, const std::vector<ReqSpec> &reqs, const sieve_t
                    unsigned long long *counts, uint32_t ncounts, cudaStream_t st, int reps)
 {
     std::unique_ptr<Plan> P = build_plan(c, reqs, t);
-    if (P->pool_entries > c->scr.pool_entries) return 1e30;
+    if (!P || P->pool_entries > c->scr.pool_entries) return 1e30;
     if (run_plan_n(c, P.get(), out, counts, ncounts, st, false) != SIEVE_OK) return 1e30;
     Timer tm;
     double best = 1e30;
@@ -107,7 +107,7 @@ sieve_tuning descend(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tunin
 
 sieve_status sieve_autotune(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, sieve_tuning *out,
                             sieve_stream stream)
-{
+try {
     if (!c || l < 5 || l > 40 || n == 0) return SIEVE_EINVAL;
     if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
     const uint64_t j0 = f << l, nbits = n << l;
@@ -133,11 +133,13 @@ sieve_status sieve_autotune(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, si
     c->tune[cls] = best;
     if (out) *out = best;
     return cudaGetLastError() == cudaSuccess ? SIEVE_OK : SIEVE_ECUDA;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }
 
 sieve_status sieve_autotune_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t count, uint32_t *dev_arena,
                                   uint64_t *dev_counts, sieve_tuning *out, sieve_stream stream)
-{
+try {
     if (!c || !reqs || !count || !dev_arena || !dev_counts) return SIEVE_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) return SIEVE_ECUDA;
     std::vector<ReqSpec> rs(count);
@@ -161,4 +163,6 @@ sieve_status sieve_autotune_batch(sieve_ctx *c, const sieve_req *reqs, uint32_t 
     c->plans.clear();
     if (out) *out = best;
     return cudaGetLastError() == cudaSuccess ? SIEVE_OK : SIEVE_ECUDA;
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }

@@ -246,3 +246,11 @@ def test_rejects_bad_arguments(S):
         S.sieve_plan_describe(PRIMES, MAX_V, 152, [(MAX_V, 1 << 20, 0)], TUNE, records=False)
     assert e.value.status == 2
     assert S.sieve_plan_describe(PRIMES, MAX_V, 152, [], TUNE)["info"]["ntiles"] == 0
+
+
+def test_plans_beyond_32_bit_tile_indices_are_refused(S):
+    # 2^43 bits in 2^12-bit tiles = 2^31 tiles: refused before anything is allocated
+    t = dict(TUNE, tile_log2=12)
+    with pytest.raises(S.SieveError) as e:
+        S.sieve_plan_describe(PRIMES, MAX_V, 152, [(0, 1 << 43, 0)], t, records=False)
+    assert e.value.status == 2
