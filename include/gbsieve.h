@@ -22,7 +22,9 @@
  * tiles returns SIEVE_ERANGE; host allocation failures return SIEVE_ENOMEM (no C++
  * exception crosses this interface).  No kernel waits on another CTA or launch, so
  * no device wait can hang.  Functions are not thread-safe on one context, except
- * the server functions, which lock.
+ * the server functions, which lock.  Calls on one context may be issued on different
+ * streams: the context's device work runs one call after another (each starts after
+ * the previous call's), since all of it shares the context's bucket pools.
  */
 #ifndef GBSIEVE_H
 #define GBSIEVE_H

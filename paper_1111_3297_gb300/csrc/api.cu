@@ -603,9 +603,9 @@ sieve_status upload_plan(sieve_ctx *c, Plan *P, cudaStream_t st)
     return s;
 }
 
-static void prof_mark(sieve_ctx *c, int kind, cudaStream_t st, bool begin)
+static void prof_mark(sieve_ctx *c, bool on, int kind, cudaStream_t st, bool begin)
 {
-    if (!c->prof) return;
+    if (!on) return;
     if (begin) {
         ProfRec r;
         r.kind = kind;
@@ -628,7 +628,10 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
 {
     const uint32_t bt = P->tune.tile_log2;
     const uint32_t tgrid_max = (uint32_t)(c->nsm * tile_blocks_per_sm(bt));
-    cudaStream_t st = scr.s_tile, ss = c->prof && c->prof_serial ? scr.s_tile : scr.s_scat;
+    // profiling covers the context's own plans, not server lanes (their own scratch,
+    // enqueued from the server's thread)
+    const bool prof = c->prof && &scr == &c->scr;
+    cudaStream_t st = scr.s_tile, ss = prof && c->prof_serial ? scr.s_tile : scr.s_scat;
     CK(cudaEventRecord(scr.ev_fork, ls));
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
     CK(cudaStreamWaitEvent(ss, scr.ev_fork, 0));
@@ -665,10 +668,10 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.ovf_cap = scr.ovf_cap;
             sa.err = scr.d_err;
             sa.tile_log2 = bt;
-            prof_mark(c, SIEVE_K_SCATTER, ss, true);
+            prof_mark(c, prof, SIEVE_K_SCATTER, ss, true);
             CK(launch_scatter(sa, e.nc, P->big_wheel, P->run_scatter, ss));
-            prof_mark(c, SIEVE_K_SCATTER, ss, false);
-            if (c->prof) CK(launch_sum_u32(scr.d_bkt_cnt[b], e.ntiles, scr.d_acc + 1, ss));
+            prof_mark(c, prof, SIEVE_K_SCATTER, ss, false);
+            if (prof) CK(launch_sum_u32(scr.d_bkt_cnt[b], e.ntiles, scr.d_acc + 1, ss));
             CK(cudaEventRecord(scr.ev_scat[b], ss));
             CK(cudaStreamWaitEvent(st, scr.ev_scat[b], 0));
         }
@@ -704,17 +707,17 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         }
         // host output: the slot's previous copy must be done before the tiles overwrite it
         if (P->host_out && ei >= 2) CK(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
-        prof_mark(c, SIEVE_K_TILE, st, true);
+        prof_mark(c, prof, SIEVE_K_TILE, st, true);
         CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));
-        prof_mark(c, SIEVE_K_TILE, st, false);
+        prof_mark(c, prof, SIEVE_K_TILE, st, false);
         CK(cudaEventRecord(scr.ev_tile[b], st));
         if (P->host_out) {
             CK(cudaEventRecord(c->ev_stage[b], st));
             CK(cudaStreamWaitEvent(c->copy_stream, c->ev_stage[b], 0));
-            prof_mark(c, SIEVE_K_COPY, c->copy_stream, true);
+            prof_mark(c, prof, SIEVE_K_COPY, c->copy_stream, true);
             CK(cudaMemcpyAsync(P->host_dst + P->ep_word0[ei], out + (size_t)b * P->slot_words,
                                P->ep_words[ei] * 4, cudaMemcpyDeviceToHost, c->copy_stream));
-            prof_mark(c, SIEVE_K_COPY, c->copy_stream, false);
+            prof_mark(c, prof, SIEVE_K_COPY, c->copy_stream, false);
             CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
         }
     }
@@ -722,7 +725,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     CK(cudaStreamWaitEvent(st, scr.ev_join, 0));
     CK(cudaEventRecord(scr.ev_join, st));
     CK(cudaStreamWaitEvent(ls, scr.ev_join, 0));
-    if (c->prof) {
+    if (prof) {
         c->prof_acc.tiles += P->tiles.size();
         c->prof_acc.bits += P->bits;
         for (const auto &g : P->groups) c->prof_acc.prime_reads += (uint64_t)(g.p_hi - g.p_lo) * g.nsu;
@@ -740,9 +743,13 @@ sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long
         s = upload_plan(c, P, st);
         if (s) return s;
     }
+    // every plan of the context shares its scratch (bucket pools, counters), so its
+    // work starts after the previous plan's, whichever streams the two were issued on
+    CK(cudaStreamWaitEvent(st, c->ev_last, 0));
     const bool graph = allow_graph && !c->prof;
     if (graph && P->exec && P->g_out == out && P->g_counts == counts && P->g_gen == c->scr.gen) {
         CK(cudaGraphLaunch(P->exec, st));
+        CK(cudaEventRecord(c->ev_last, st));
         P->runs++;
         return SIEVE_OK;
     }
@@ -765,10 +772,12 @@ sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long
         P->g_counts = counts;
         P->g_gen = c->scr.gen;
         CK(cudaGraphLaunch(P->exec, st));
+        CK(cudaEventRecord(c->ev_last, st));
         P->runs++;
         return SIEVE_OK;
     }
     s = enqueue_plan(c, c->scr, P, out, counts, ncounts, st);
+    if (!s) CK(cudaEventRecord(c->ev_last, st));
     P->runs++;
     return s;
 }
@@ -945,6 +954,7 @@ try {
         CK(cudaEventCreateWithFlags(&c->ev_stage[i], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming));
     }
+    CK(cudaEventCreateWithFlags(&c->ev_last, cudaEventDisableTiming));
     for (uint32_t k = 0; k < SIEVE_TUNE_CLASSES; ++k) c->tune[k] = default_tuning(k);
     s = build_base(c.get(), c->cap_stream);
     if (s) {
@@ -975,6 +985,7 @@ void sieve_destroy(sieve_ctx *c)
         if (c->ev_stage[i]) cudaEventDestroy(c->ev_stage[i]);
         if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     }
+    if (c->ev_last) cudaEventDestroy(c->ev_last);
     for (auto &r : c->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1110,9 +1121,9 @@ sieve_status sieve_count(sieve_ctx *c, const uint32_t *dev_bits, uint64_t nbits,
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(c->scr.d_acc, 0, 8, st));
     if (nbits) {
-        prof_mark(c, SIEVE_K_COUNT, st, true);
+        prof_mark(c, c->prof, SIEVE_K_COUNT, st, true);
         CK(launch_popcount(dev_bits, nbits / 32, c->scr.d_acc, (uint32_t)(c->nsm * 4), st));
-        prof_mark(c, SIEVE_K_COUNT, st, false);
+        prof_mark(c, c->prof, SIEVE_K_COUNT, st, false);
     }
     CK(cudaMemcpyAsync(c->h_acc, c->scr.d_acc, 8, cudaMemcpyDeviceToHost, st));
     sieve_status s = take_device_error(c, st);  // synchronises the stream

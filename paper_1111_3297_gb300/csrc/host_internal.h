@@ -131,6 +131,7 @@ struct sieve_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_stage[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_last = nullptr;  // end of the last plan's device work (plans share the scratch)
     sieve_tuning batch_tune{};   // autotuned tuning for batches (tile_log2 == 0: class default)
     // staging for the host-output path
     uint32_t *d_stage = nullptr;

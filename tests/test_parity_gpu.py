@@ -212,6 +212,40 @@ def test_graph_replay_is_identical(ctx):
         assert np.array_equal(o, want)
 
 
+def test_calls_on_two_streams_share_the_scratch_safely(ctx):
+    """Two intervals issued back to back on two streams with no wait between them, three
+    times (direct, captured, replayed).  Every plan of a context shares its bucket pools
+    and counters, so each table must still equal the one computed alone."""
+    saved = [S.sieve_get_tuning(ctx, k) for k in range(4)]
+    try:
+        for k in range(4):  # eight epochs of 128 tiles per interval: both pools reused often
+            S.sieve_set_tuning(ctx, k, tile_log2=20, presieve_groups=2, coop_max=4096,
+                               medium_max=1 << 19, window_tiles=128, epoch_tiles=128)
+        l, n = 20, 1024
+        fs = ((10**15 >> 21) - 512, (10**16 >> 21) - 512)
+        want = []
+        for f in fs:
+            w = torch.empty((n << l) // 32, dtype=torch.int32, device="cuda")
+            S.sieve_segments(ctx, l, f, n, w)
+            S.sieve_sync(ctx)
+            want.append(w)
+        streams = (torch.cuda.Stream(), torch.cuda.Stream())
+        outs = [torch.empty_like(w) for w in want]
+        for _ in range(3):
+            for o in outs:
+                o.fill_(-1)
+            torch.cuda.synchronize()
+            for f, o, st in zip(fs, outs, streams):
+                S.sieve_segments(ctx, l, f, n, o, stream=st)
+            for st in streams:
+                S.sieve_sync(ctx, st)
+            for o, w in zip(outs, want):
+                assert torch.equal(o, w)
+    finally:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **saved[k])
+
+
 def test_argument_errors(ctx):
     out = torch.empty(1 << 10, dtype=torch.int32, device="cuda")
     with pytest.raises(S.SieveError) as e:
