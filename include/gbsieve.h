@@ -310,6 +310,11 @@ sieve_status sieve_plan_describe(const uint32_t *host_primes, uint64_t nprimes, 
  * bucket pools stay resident.  Results are read with sieve_server_poll: the
  * composite count, a device pointer to the request's table inside the server's
  * memory (valid until sieve_server_release) and the completion time.
+ * mem_cap >= 256 MiB and 1 <= max_inflight <= 16, else SIEVE_EINVAL.  Each batch
+ * runs on a scratch of its own (two bucket pools of mem_cap / (32 * max_inflight)
+ * slots, at most 2^29), so the server's work never waits on the context's other
+ * calls. The scheduler reads the context's tunings, so sieve_set_tuning and
+ * the autotuners must not run while a server on the context is live.
  */
 typedef struct sieve_server sieve_server;
 typedef struct {
