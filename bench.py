@@ -2,8 +2,9 @@
 
 Default workload (one GPU): l=20, n=8192 segments (2^34 consecutive numbers,
 2^33 odd ones) with the midpoint at 10^15, the paper's (l, f, n) interface.
---workload c3 runs l=20, n=32768 around 2^60 (the large-prime-dominated case);
---workload batch runs the 4096 seeded requests of uneven length and magnitude.
+--workload c3 runs l=20, n=32768 around 2^60 (the large-prime-dominated case).
+Beside the workload, the batched-vs-plain measurement runs 4096 seeded requests of
+uneven length and magnitude (--batch-requests), then serving and a midpoint sweep.
 Under torchrun each rank sieves its own interval of the same size (the next n
 segments): weak scaling, no collective on the data path.
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--segments", type=int, default=0, help="override n (small profiling cases)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--batch-requests", type=int, default=4096,
+                    help="requests in the batched-vs-plain measurement (fewer for profiling cases)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1e12..1e18 midpoint sweep")
@@ -282,12 +285,12 @@ def measure_sweep(S, ctx, hbm_peak, r_atom):
 
 
 def measure_batch(S, ctx, args, rank, world):
-    """4096 seeded requests of uneven length (2^16..2^28 numbers) and magnitude
+    """args.batch_requests (4096) seeded requests of uneven length (2^16..2^28 numbers) and magnitude
     (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
     plain form (one sieve_segments call per request), same outputs, same GPU."""
     import torch
     from paper_1111_3297_gb300 import workloads
-    reqs = workloads.batch_requests(4096, seed=rank)
+    reqs = workloads.batch_requests(args.batch_requests, seed=rank)
     lay, off = [], 0
     for j0, nb in reqs:
         lay.append((j0, nb, off))
