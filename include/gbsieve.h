@@ -53,6 +53,11 @@ typedef enum {
 /* Text for a status code (static storage). */
 const char *sieve_strerror(sieve_status s);
 
+/* For SIEVE_ECUDA: the failed CUDA runtime call and its error text, as seen by the
+ * last failing call on this host thread ("" if none).  Storage belongs to the
+ * library, per thread, until that thread's next failing call. */
+const char *sieve_last_cuda_error(void);
+
 /*
  * Create a context on CUDA device `device`, able to sieve any interval whose
  * largest number is <= max_v.  Builds the base of Sec. 1.4 (Definition "base":

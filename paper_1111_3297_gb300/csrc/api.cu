@@ -113,6 +113,8 @@ void build_big_wheel(std::vector<uint32_t> &gapw, std::vector<uint32_t> &rstate,
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+const char *sieve_last_cuda_error(void) { return gbs::g_last_cuda_error; }
+
 const char *sieve_strerror(sieve_status s)
 {
     switch (s) {
@@ -128,6 +130,7 @@ const char *sieve_strerror(sieve_status s)
     return "unknown status";
 }
 
+// a failed CUDA runtime call: its text is kept for sieve_last_cuda_error (per thread)
 #define CK(call)                                                                      \
     do {                                                                              \
         cudaError_t e_ = (call);                                                      \
@@ -139,7 +142,7 @@ const char *sieve_strerror(sieve_status s)
     } while (0)
 
 namespace gbs {
-char g_last_cuda_error[512];
+thread_local char g_last_cuda_error[512];
 
 uint32_t prime_count_le(const sieve_ctx *c, uint64_t x)
 {

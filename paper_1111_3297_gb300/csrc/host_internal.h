@@ -147,7 +147,7 @@ struct sieve_ctx {
 };
 
 namespace gbs {
-extern char g_last_cuda_error[512];
+extern thread_local char g_last_cuda_error[512];
 uint64_t isqrt_u64(uint64_t x);
 uint32_t prime_count_le(const sieve_ctx *c, uint64_t x);
 double inv_sum(const sieve_ctx *c, uint32_t a, uint32_t b);

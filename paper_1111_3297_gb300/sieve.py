@@ -24,7 +24,10 @@ K_TILE, K_SCATTER, K_COUNT, K_RESET, K_COPY = 0, 1, 2, 3, 4
 class SieveError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), lib().sieve_strerror(status).decode()))
+        msg = "%s: %s (%s)" % (where, STATUS.get(status, status), lib().sieve_strerror(status).decode())
+        if status == 4:  # SIEVE_ECUDA: name the failed runtime call
+            msg += ": " + lib().sieve_last_cuda_error().decode(errors="replace")
+        super().__init__(msg)
 
 
 class Tuning(ctypes.Structure):
@@ -84,6 +87,7 @@ def lib():
         L = ctypes.CDLL(_LIBPATH)
         sig = {
             "sieve_strerror": (ctypes.c_char_p, [_i32]),
+            "sieve_last_cuda_error": (ctypes.c_char_p, []),
             "sieve_init": (_i32, [ctypes.POINTER(_vp), _i32, _u64, ctypes.c_size_t]),
             "sieve_destroy": (None, [_vp]),
             "sieve_segments": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp]),

@@ -49,6 +49,8 @@ def test_host_only_entry_points_work_without_a_gpu(lib):
     lib.sieve_strerror.restype = ctypes.c_char_p
     assert lib.sieve_strerror(0) == b"ok"
     assert b"overflow" in lib.sieve_strerror(7)
+    lib.sieve_last_cuda_error.restype = ctypes.c_char_p
+    assert isinstance(lib.sieve_last_cuda_error(), bytes)
     f = ctypes.c_uint64()
     lib.sieve_f_from_midpoint.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint64)]
