@@ -137,12 +137,29 @@ def _stream(stream):
     return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _dev_ptr(t, what):
+def _nbytes(t):
+    return t.numel() * t.element_size() if hasattr(t, "element_size") else t.nbytes
+
+
+def _dev_ptr(t, what, need=0):
+    """Device address of a contiguous CUDA tensor holding at least `need` bytes (the
+    library takes plain pointers and cannot see the size: a short buffer would be
+    written past its end)."""
     if not (hasattr(t, "is_cuda") and t.is_cuda):
         raise TypeError("%s must be a CUDA tensor" % what)
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % what)
+    if _nbytes(t) < need:
+        raise ValueError("%s holds %d bytes, the call needs %d" % (what, _nbytes(t), need))
     return _vp(t.data_ptr())
+
+
+def _table_bytes(l, n):
+    return (int(n) << int(l)) // 8 if 0 <= int(l) < 64 else 0
+
+
+def _batch_bytes(reqs):
+    return max([(int(r[2]) + int(r[1]) // 32) * 4 for r in reqs] or [0])
 
 
 class Ctx:
@@ -175,7 +192,8 @@ def sieve_destroy(ctx):
 
 
 def sieve_segments(ctx, l, f, n, dev_bits, stream=None):
-    _check(lib().sieve_segments(ctx.handle, l, f, n, _dev_ptr(dev_bits, "dev_bits"), _stream(stream)),
+    _check(lib().sieve_segments(ctx.handle, l, f, n, _dev_ptr(dev_bits, "dev_bits", _table_bytes(l, n)),
+                                _stream(stream)),
            "sieve_segments")
 
 
@@ -186,7 +204,7 @@ def sieve_f_from_midpoint(l, n, mant, exp10):
 
 
 def sieve_segments_midpoint(ctx, l, mant, exp10, n, dev_bits, stream=None):
-    _check(lib().sieve_segments_midpoint(ctx.handle, l, mant, exp10, n, _dev_ptr(dev_bits, "dev_bits"),
+    _check(lib().sieve_segments_midpoint(ctx.handle, l, mant, exp10, n, _dev_ptr(dev_bits, "dev_bits", _table_bytes(l, n)),
                                          _stream(stream)), "sieve_segments_midpoint")
 
 
@@ -197,13 +215,17 @@ def sieve_segments_host(ctx, l, f, n, host_bits, stream=None):
             raise TypeError("host_bits must be a contiguous CPU tensor")
         ptr = host_bits.data_ptr()
     else:
+        if not host_bits.flags["C_CONTIGUOUS"]:
+            raise TypeError("host_bits must be a contiguous array")
         ptr = host_bits.ctypes.data
+    if _nbytes(host_bits) < _table_bytes(l, n):
+        raise ValueError("host_bits holds %d bytes, the call needs %d" % (_nbytes(host_bits), _table_bytes(l, n)))
     _check(lib().sieve_segments_host(ctx.handle, l, f, n, _vp(ptr), _stream(stream)), "sieve_segments_host")
 
 
 def sieve_count(ctx, dev_bits, nbits, stream=None):
     out = _u64()
-    _check(lib().sieve_count(ctx.handle, _dev_ptr(dev_bits, "dev_bits"), nbits, ctypes.byref(out),
+    _check(lib().sieve_count(ctx.handle, _dev_ptr(dev_bits, "dev_bits", int(nbits) // 8), nbits, ctypes.byref(out),
                              _stream(stream)), "sieve_count")
     return out.value
 
@@ -222,8 +244,8 @@ def _reqs(reqs):
 def sieve_batch(ctx, reqs, dev_arena, dev_counts, stream=None):
     """reqs: sequence of (j0, nbits, out_word_off); dev_counts: CUDA int64 tensor (len(reqs),)."""
     arr = _reqs(reqs)
-    _check(lib().sieve_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena"),
-                             _dev_ptr(dev_counts, "dev_counts"), _stream(stream)), "sieve_batch")
+    _check(lib().sieve_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena", _batch_bytes(reqs)),
+                             _dev_ptr(dev_counts, "dev_counts", 8 * len(reqs)), _stream(stream)), "sieve_batch")
 
 
 def sieve_get_tuning(ctx, cls):
@@ -249,8 +271,9 @@ def sieve_autotune(ctx, l, f, n, stream=None):
 def sieve_autotune_batch(ctx, reqs, dev_arena, dev_counts, stream=None):
     t = Tuning()
     arr = _reqs(reqs)
-    _check(lib().sieve_autotune_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena"),
-                                      _dev_ptr(dev_counts, "dev_counts"), ctypes.byref(t), _stream(stream)),
+    _check(lib().sieve_autotune_batch(ctx.handle, arr, len(reqs), _dev_ptr(dev_arena, "dev_arena", _batch_bytes(reqs)),
+                                      _dev_ptr(dev_counts, "dev_counts", 8 * len(reqs)), ctypes.byref(t),
+                                      _stream(stream)),
            "sieve_autotune_batch")
     return t.as_dict()
 

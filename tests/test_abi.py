@@ -74,3 +74,46 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(S, "_LIBPATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         S.lib()
+
+
+class _FakeCudaTensor:
+    """Looks like a contiguous CUDA int32 tensor of n elements to the binding."""
+    is_cuda = True
+
+    def __init__(self, n):
+        self.n = n
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self.n
+
+    def element_size(self):
+        return 4
+
+    def data_ptr(self):
+        return 0x10000
+
+
+class _FakeCtx:
+    handle = None
+
+
+def test_binding_refuses_buffers_smaller_than_the_call(lib):
+    # the C ABI takes plain pointers; the binding checks sizes before any call
+    import numpy as np
+    from paper_1111_3297_gb300 import sieve as S
+    with pytest.raises(ValueError):  # 2^20 bits need 2^15 words
+        S.sieve_segments(_FakeCtx(), 20, 0, 1, _FakeCudaTensor((1 << 15) - 1))
+    with pytest.raises(ValueError):
+        S.sieve_segments_midpoint(_FakeCtx(), 20, 1, 15, 2, _FakeCudaTensor(1 << 15))
+    with pytest.raises(ValueError):
+        S.sieve_count(_FakeCtx(), _FakeCudaTensor(8), 8 * 32 + 32)
+    reqs = [(0, 64, 0), (1 << 20, 96, 10)]  # the second ends at word 13
+    with pytest.raises(ValueError):
+        S.sieve_batch(_FakeCtx(), reqs, _FakeCudaTensor(12), _FakeCudaTensor(4))
+    with pytest.raises(ValueError):  # two int64 counts need 16 bytes
+        S.sieve_batch(_FakeCtx(), reqs, _FakeCudaTensor(13), _FakeCudaTensor(3))
+    with pytest.raises(ValueError):
+        S.sieve_segments_host(_FakeCtx(), 10, 0, 4, np.zeros(127, dtype=np.uint32))

@@ -255,8 +255,10 @@ def test_argument_errors(ctx):
         S.sieve_segments(ctx, 10, 0, 0, out)
     assert e.value.status == 1
     with pytest.raises(S.SieveError) as e:  # numbers beyond 2^64
-        S.sieve_segments(ctx, 20, 1 << 43, 1, out)
+        S.sieve_segments(ctx, 20, 1 << 43, 1, torch.empty(1 << 15, dtype=torch.int32, device="cuda"))
     assert e.value.status == 2
+    with pytest.raises(ValueError):  # a table larger than the buffer never reaches the library
+        S.sieve_segments(ctx, 20, 0, 1, out)
     with pytest.raises(S.SieveError) as e:  # sqrt beyond the context's base (2^31)
         S.sieve_segments(ctx, 5, (1 << 58) - 1, 1, out)
     assert e.value.status == 2
