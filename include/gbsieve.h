@@ -107,7 +107,10 @@ sieve_status sieve_segments_host(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_
  * Number of 1 bits (composites) in the first nbits bits of the device table
  * dev_bits (nbits % 32 == 0).  Waits for `stream` and writes *host_count.
  * Primes in the table's range = nbits - composites - (1 if the table starts at
- * the number 1, since 1 is neither).
+ * the number 1, since 1 is neither): the prime count of the interval that the table of
+ * Definition "Sieve table, Segments" (Sec. 1.3) encodes.  SIEVE_EINVAL for a null
+ * pointer or nbits not a multiple of 32; a device error recorded since the last wait
+ * is returned here (the count is then not meaningful).
  */
 sieve_status sieve_count(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t nbits,
                          uint64_t *host_count, sieve_stream stream);
@@ -150,6 +153,9 @@ typedef struct {
     uint64_t nbits;
     uint64_t out_word_off;
 } sieve_req;
+/* Errors: SIEVE_EINVAL (null pointers with count > 0, a request not word aligned or
+ * empty), SIEVE_ERANGE (a request beyond 2^64 or the context's base, or more than 2^31
+ * tiles in all); nothing is enqueued then.  Requests may not overlap in the arena. */
 
 sieve_status sieve_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t count,
                          uint32_t *dev_arena, uint64_t *dev_counts, sieve_stream stream);
@@ -179,7 +185,8 @@ typedef struct {
     uint32_t epoch_tiles;
 } sieve_tuning;
 
-/* Tuning classes: by the magnitude of the interval's largest number. */
+/* Tuning classes: by the magnitude of the interval's largest number.  cls must be
+ * below SIEVE_TUNE_CLASSES (else SIEVE_EINVAL). */
 #define SIEVE_TUNE_CLASSES 4 /* < 2^40, < 2^50, < 2^56, >= 2^56 */
 sieve_status sieve_get_tuning(sieve_ctx *ctx, uint32_t cls, sieve_tuning *out);
 /* Replaces the tuning of class cls (SIEVE_EINVAL if out of range); it also drops a
@@ -205,7 +212,10 @@ sieve_status sieve_autotune_batch(sieve_ctx *ctx, const sieve_req *host_reqs, ui
                                   uint32_t *dev_arena, uint64_t *dev_counts, sieve_tuning *out,
                                   sieve_stream stream);
 
-/* Base primes resident in the context (device pointer, ascending) and their count. */
+/* The base of Sec. 1.4 (Definition "base") resident in the context: *dev_primes
+ * receives a device pointer to the odd primes 3 <= p <= *limit in ascending order
+ * (owned by the context, valid until sieve_destroy; do not write), *count their
+ * number, *limit = isqrt of the context's max_v (capped at 2^32 - 1). */
 sieve_status sieve_base_info(sieve_ctx *ctx, const uint32_t **dev_primes, uint64_t *count,
                              uint64_t *limit);
 
@@ -333,12 +343,19 @@ typedef struct {
 
 sieve_status sieve_server_create(sieve_ctx *ctx, size_t mem_cap, uint32_t max_inflight,
                                  sieve_server **srv);
+/* Queue one request (bit indices j0 .. j0+nbits-1, word aligned as for sieve_batch);
+ * *id identifies it in the results.  SIEVE_EINVAL / SIEVE_ERANGE as for sieve_batch,
+ * SIEVE_ENOMEM when its table could never fit the server's memory, SIEVE_EBUSY once
+ * the server is stopping. */
 sieve_status sieve_server_submit(sieve_server *srv, uint64_t j0, uint64_t nbits, uint64_t *id);
 /* Up to max results that completed since the last poll; *n receives how many.
  * timeout_ms > 0 waits (bounded) for at least one. */
 sieve_status sieve_server_poll(sieve_server *srv, sieve_result *out, uint32_t max, uint32_t *n,
                                uint32_t timeout_ms);
+/* Return a polled result's table memory to the server (SIEVE_EINVAL for an id that is
+ * unknown, already released or not yet completed). */
 sieve_status sieve_server_release(sieve_server *srv, uint64_t id);
+/* Seconds on the server's monotonic clock (the clock of the result timestamps). */
 double sieve_server_now(sieve_server *srv);
 /* Stop the scheduler after the requests already submitted have completed. */
 void sieve_server_destroy(sieve_server *srv);
