@@ -153,8 +153,8 @@ typedef struct {
     uint64_t nbits;
     uint64_t out_word_off;
 } sieve_req;
-/* Errors: SIEVE_EINVAL (null pointers with count > 0, a request not word aligned or
- * empty), SIEVE_ERANGE (a request beyond 2^64 or the context's base, or more than 2^31
+/* Errors: SIEVE_EINVAL (null pointers with count > 0, dev_arena not 4-byte aligned, a
+ * request not word aligned or empty), SIEVE_ERANGE (a request beyond 2^64 or the context's base, or more than 2^31
  * tiles in all); nothing is enqueued then.  Requests may not overlap in the arena. */
 
 sieve_status sieve_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t count,
@@ -215,7 +215,8 @@ sieve_status sieve_autotune_batch(sieve_ctx *ctx, const sieve_req *host_reqs, ui
 /* The base of Sec. 1.4 (Definition "base") resident in the context: *dev_primes
  * receives a device pointer to the odd primes 3 <= p <= *limit in ascending order
  * (owned by the context, valid until sieve_destroy; do not write), *count their
- * number, *limit = isqrt of the context's max_v (capped at 2^32 - 1). */
+ * number, *limit = isqrt of the context's max_v (capped at 2^32 - 1).  Any of the
+ * three pointers may be NULL. */
 sieve_status sieve_base_info(sieve_ctx *ctx, const uint32_t **dev_primes, uint64_t *count,
                              uint64_t *limit);
 
