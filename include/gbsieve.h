@@ -263,8 +263,10 @@ sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s);
  *                memory, nprimes of them; the caller vouches for completeness,
  *                only order, oddness and the bound are checked);
  *   nsm          SMs to plan chunks for (1..1024);
- *   t            tuning (ranges as for sieve_set_tuning); NULL = the default of
- *                the largest request's class;
+ *   t            tuning (ranges as for sieve_set_tuning); NULL = what a fresh context
+ *                takes: for one request sieve_segments' choice (the class default,
+ *                with smaller tiles when the interval has fewer than 4 per SM),
+ *                else the default of the largest request's class;
  *   pool_entries bucket slots per epoch (>= 4096, at most 2^32 - 2^22).
  *                sieve_init's contexts have mem_budget / 8 of them.
  * *info receives the counts.  tiles / groups / chunks may each be NULL; otherwise

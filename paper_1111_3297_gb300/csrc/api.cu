@@ -1266,7 +1266,9 @@ try {
         vmax = std::max(vmax, vl[r]);
     }
     std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
-    const sieve_tuning t = tp ? *tp : default_tuning(tune_class(vmax));
+    for (uint32_t k = 0; k < SIEVE_TUNE_CLASSES; ++k) c.tune[k] = default_tuning(k);
+    // no tuning given: what a fresh context takes (sieve_segments' for one interval)
+    const sieve_tuning t = tp ? *tp : count == 1 ? tuning_for(&c, vl[0], reqs[0].nbits) : c.tune[tune_class(vmax)];
     std::unique_ptr<Plan> P = build_plan(&c, rs, t, pool_entries);
     if (!P) return SIEVE_ERANGE;
 

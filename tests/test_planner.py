@@ -248,6 +248,19 @@ def test_rejects_bad_arguments(S):
     assert S.sieve_plan_describe(PRIMES, MAX_V, 152, [], TUNE)["info"]["ntiles"] == 0
 
 
+def test_short_intervals_get_smaller_tiles_without_a_tuning(S):
+    # sieve_segments' rule on a fresh context: halve the tile (down to 2^14 bits) while
+    # the interval has fewer than 4 tiles per SM
+    nsm = 152
+    for nbits in (1 << 20, 1 << 26, 1 << 30, 1 << 31):
+        info = S.sieve_plan_describe(PRIMES, MAX_V, nsm, [(1 << 40, nbits, 0)], None, records=False)["info"]
+        tiles = info["ntiles"]
+        bt = (nbits // tiles).bit_length() - 1
+        assert nbits == tiles << bt
+        assert bt == 14 or tiles >= 4 * nsm
+        assert bt == 20 or (nbits >> (bt + 1)) < 4 * nsm
+
+
 def test_plans_beyond_32_bit_tile_indices_are_refused(S):
     # 2^43 bits in 2^12-bit tiles = 2^31 tiles: refused before anything is allocated
     t = dict(TUNE, tile_log2=12)
