@@ -360,7 +360,9 @@ sieve_status sieve_server_poll(sieve_server *srv, sieve_result *out, uint32_t ma
 sieve_status sieve_server_release(sieve_server *srv, uint64_t id);
 /* Seconds on the server's monotonic clock (the clock of the result timestamps). */
 double sieve_server_now(sieve_server *srv);
-/* Stop the scheduler after the requests already submitted have completed. */
+/* Stop the scheduler after the requests already submitted have completed.  Requests
+ * still queued whose tables can no longer fit (the arena is held by results that were
+ * not released) end with SIEVE_EBUSY instead, so this call always returns. */
 void sieve_server_destroy(sieve_server *srv);
 
 #ifdef __cplusplus

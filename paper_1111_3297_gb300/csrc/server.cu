@@ -79,6 +79,7 @@ struct Req {
     uint64_t composites = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     int status = SIEVE_OK;
+    bool admitted = false;  // its table holds arena memory
     bool done = false;
 };
 
@@ -211,6 +212,7 @@ void sieve_server::loop()
                 while (!pending.empty() && batch.size() < kMaxBatch && bits < kMaxBatchBits) {
                     Req *r = pending.front();
                     if (!arena.alloc(r->bytes, &r->off)) break;  // wait for memory
+                    r->admitted = true;
                     pending.pop_front();
                     r->t_admit = now();
                     bits += r->nbits;
@@ -225,7 +227,29 @@ void sieve_server::loop()
         std::unique_lock<std::mutex> g(mu);
         bool any_busy = false;
         for (Lane &L : lanes) any_busy |= L.busy;
-        if (stop && pending.empty() && !any_busy) break;
+        if (stop && !any_busy) {
+            if (pending.empty()) break;
+            if (!launched) {
+                // stopping, nothing in flight, and the head of the queue did not fit
+                uint64_t o = 0;
+                if (arena.alloc(pending.front()->bytes, &o)) {
+                    arena.release(o, pending.front()->bytes);
+                    continue;  // a table was released meanwhile: admit on the next pass
+                }
+                // only the client's release of held tables could make room, so the
+                // queued requests end now instead of holding destroy forever
+                const double t = now();
+                for (Req *r : pending) {
+                    r->status = SIEVE_EBUSY;
+                    r->t_done = t;
+                    r->done = true;
+                    done_q.push_back(r);
+                }
+                pending.clear();
+                cv_done.notify_all();
+                break;
+            }
+        }
         if (!launched) {
             if (any_busy)
                 cv_work.wait_for(g, std::chrono::microseconds(50));
@@ -336,7 +360,7 @@ try {
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->live.find(id);
     if (it == S->live.end() || !it->second->done) return SIEVE_EINVAL;
-    S->arena.release(it->second->off, it->second->bytes);
+    if (it->second->admitted) S->arena.release(it->second->off, it->second->bytes);
     delete it->second;
     S->live.erase(it);
     S->cv_work.notify_one();

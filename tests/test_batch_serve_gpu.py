@@ -160,6 +160,27 @@ def test_serving_results_equal_alone_and_in_the_mix(ctx):
         srv.close()
 
 
+def test_server_destroy_returns_when_held_tables_block_the_queue(ctx):
+    """A served result that is never released keeps its table in the arena.  A queued
+    request that cannot fit beside it must not hold sieve_server_destroy forever: it
+    ends with SIEVE_EBUSY and destroy returns."""
+    srv = S.Server(ctx, mem_cap=256 << 20, max_inflight=2)  # 192 MiB of table arena
+    try:
+        nb = 1 << 30  # 128 MiB of table each
+        first = srv.submit(1 << 40, nb)
+        got, deadline = [], time.time() + 120
+        while not got and time.time() < deadline:
+            got = srv.poll(8, timeout_ms=500)
+        assert len(got) == 1 and got[0]["id"] == first and got[0]["status"] == 0
+        srv.submit((1 << 40) + nb, nb)  # does not fit while the first table is held
+        time.sleep(0.2)
+        assert srv.poll(8) == []
+    finally:
+        t0 = time.time()
+        srv.close()
+        assert time.time() - t0 < 60
+
+
 def test_batch_with_epochs_longer_than_2p32_bits(ctx):
     """Two long requests through the multi-request scatter with epochs of 8192 tiles of
     2^20 bits (2^33 bits): the next hits carried between its groups are 32-bit offsets,
