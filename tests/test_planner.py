@@ -267,3 +267,25 @@ def test_plans_beyond_32_bit_tile_indices_are_refused(S):
     with pytest.raises(S.SieveError) as e:
         S.sieve_plan_describe(PRIMES, MAX_V, 152, [(0, 1 << 43, 0)], t, records=False)
     assert e.value.status == 2
+
+
+def test_random_plans_keep_the_invariants(S):
+    # seeded random batches, tunings and pool sizes: the plan must satisfy every
+    # invariant of check_plan whatever the mix
+    rng = np.random.default_rng(2024)
+    for case in range(40):
+        tl = int(rng.integers(12, 21))
+        win = int(min(1024, 1 << int(rng.integers(0, 11)), (1 << 30) >> tl))
+        t = dict(tile_log2=tl, presieve_groups=int(rng.integers(1, 14)),
+                 coop_max=int(1 << int(rng.integers(6, 16))), medium_max=int(1 << int(rng.integers(8, 24))),
+                 window_tiles=win, epoch_tiles=int(win * int(rng.integers(1, 9))))
+        reqs, off = [], 0
+        for _ in range(int(rng.integers(1, 60))):
+            mag = 10 ** rng.uniform(2, 15.9)
+            nb = int(rng.integers(1, 1 << int(rng.integers(1, 14)))) * 32
+            j0 = (int(mag) // 2) // 32 * 32
+            reqs.append((j0, nb, off))
+            off += nb // 32 + int(rng.integers(0, 3))
+        pool = int(1 << int(rng.integers(12, 32)))
+        plan = S.sieve_plan_describe(PRIMES, MAX_V, int(rng.integers(1, 200)), reqs, t, pool_entries=pool)
+        check_plan(plan, reqs, t, pool)
