@@ -51,3 +51,19 @@ def test_base_primes_upto_counts():
     # pi(10^k) - 1 odd primes (2 is not in the odd-only base)
     for x, pi in [(10, 4), (100, 25), (1000, 168), (10 ** 5, 9592)]:
         assert len(b.base_primes_upto(x)) == pi - 1
+
+
+def test_step_roofline_is_the_slower_of_bytes_and_marks():
+    # B_alg = N/8 + 16 H_large + 4 V bytes at the copy bandwidth, against H marks at the
+    # shared-memory atomic rate; the fraction is the roofline time over the step time
+    b = _bench()
+    N, h_large, visits, marks = 8 * 10**9, 10**8, 5 * 10**7, 4 * 10**9
+    bytes_alg = N / 8 + 16 * h_large + 4 * visits  # 2.8e9 B
+    r = b.step_roofline(N, marks, h_large, visits, 2e-3, 7000.0, 3.5e12)
+    assert r["bytes_alg"] == bytes_alg
+    t_hbm, t_atom = bytes_alg / 7e12, marks / 3.5e12  # 0.4 ms, 1.143 ms
+    assert r["bound"] == "smem_atomic"
+    assert abs(r["t_roof_ms"] - t_atom * 1e3) < 1e-12
+    assert abs(r["frac"] - t_atom / 2e-3) < 1e-12
+    r = b.step_roofline(N, marks / 100, h_large, visits, 2e-3, 7000.0, 3.5e12)
+    assert r["bound"] == "hbm" and abs(r["frac"] - t_hbm / 2e-3) < 1e-12
