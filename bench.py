@@ -222,9 +222,16 @@ def cpu_baseline(wl, f):
     t0 = time.perf_counter()
     oracle.sieve(l, f, sample, base=base, nthreads=cores)
     dt = time.perf_counter() - t0
+    # one core on a proportionally smaller sample (the same segments' start)
+    sample1 = max(1, sample // cores)
+    t0 = time.perf_counter()
+    oracle.sieve(l, f, sample1, base=base, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": (sample << l) / dt, "unit": "odd numbers/s", "cores": cores, "kind": "oracle",
             "sample": "first %d of %d segments (2^%d bits each), %.2f s on %d threads"
-                      % (sample, n, l, dt, cores)}
+                      % (sample, n, l, dt, cores),
+            "single_core": {"value": (sample1 << l) / dt1, "unit": "odd numbers/s", "cores": 1,
+                            "sample": "first %d segments, %.2f s on 1 thread" % (sample1, dt1)}}
 
 
 KERNEL_SOURCES = ("kernels.cu", "sieve_internal.cuh")  # everything compiled into the kernels
