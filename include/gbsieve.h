@@ -127,9 +127,13 @@ sieve_status sieve_count(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t nbit
  * array of partial counts inside the library, which every GPU that loads the
  * library holds until the process exits.  The first call on a device resolves
  * that array's device address (a one-time set-up with the device current); make
- * the first call on each device before any stream capture.  All calls share the
- * array and each overwrites the entries it uses, so calls that overlap on the
- * GPU (e.g. on two streams at once) race and must be ordered by the caller.
+ * the first call on each device before any stream capture.  The address is kept
+ * per device together with the id of the context it belongs to; after a device
+ * reset the next call resolves it again.  All calls share the array and each
+ * overwrites the entries it uses, so calls that overlap on the GPU (e.g. on two
+ * streams at once) race and must be ordered by the caller.  SIEVE_ECUDA names the
+ * failed step in sieve_last_cuda_error(); an error already pending on the calling
+ * thread is reported that way too, without launching, and is not cleared.
  */
 #define SIEVE_NOALLOC_MAX_BITS (1ull << 37)
 sieve_status sieve_count_noalloc(const uint32_t *dev_bits, uint64_t nbits, uint64_t *dev_count,
