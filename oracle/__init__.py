@@ -145,3 +145,42 @@ def is_prime_mr(m: int) -> bool:
 
 def get_bit(words: np.ndarray, j: int) -> int:
     return int((int(words[j >> 5]) >> (j & 31)) & 1)
+
+
+def _coprime_prefix(W: int) -> np.ndarray:
+    """pre[x] = number of odd c in [1, x] with gcd(c, W) = 1, for 0 <= x < 2W (W odd)."""
+    c = np.arange(2 * W, dtype=np.int64)
+    ok = (c % 2 == 1) & (np.gcd(c, W) == 1)
+    return np.cumsum(ok)
+
+
+def large_prime_hits(j0: int, nbits: int, primes, W: int = 1) -> int:
+    """Hits that striking with the primes `primes` emits on the bits j0 .. j0+nbits-1:
+    for each p, the odd multiples m = p*c in [max(2*j0+1, p^2), 2*(j0+nbits)-1] (Sec. 1.4:
+    from the first multiple in the interval, but never below p^2), keeping only the
+    multipliers c coprime to W (the wheel, Sec. 3.2.1; W = 1 keeps all).  By Theorem
+    thm:big and Cor. cor:complete (Sec. 2.3) every such multiple lands in exactly one
+    segment's bucket, so a method that emits each hit once emits exactly this many.
+    Closed form per prime (numpy, int64: numbers below 2^62)."""
+    p = np.asarray(primes, dtype=np.int64)
+    if len(p) == 0 or nbits == 0:
+        return 0
+    lo_num = 2 * int(j0) + 1
+    hi_num = 2 * (int(j0) + int(nbits)) - 1
+    assert hi_num < (1 << 62)
+    start = np.maximum(lo_num, p * p)
+    c1 = (start + p - 1) // p            # smallest multiplier with p*c >= start
+    c1 = c1 + (1 - c1 % 2)               # ... made odd
+    c2 = hi_num // p
+    c2 = c2 - (1 - c2 % 2)               # largest odd multiplier with p*c <= hi_num
+    ok = c1 <= c2
+    if W == 1:
+        cnt = (c2 - c1) // 2 + 1
+        return int(cnt[ok].sum())
+    pre = _coprime_prefix(W)
+    per = int(pre[-1])                   # phi(W) odd residues per period 2W
+
+    def F(x):                            # odd c in [1, x] coprime to W, x >= 0
+        return (x // (2 * W)) * per + pre[x % (2 * W)]
+    cnt = F(c2) - F(np.maximum(c1 - 1, 0))
+    return int(cnt[ok].sum())
