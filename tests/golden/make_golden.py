@@ -3,13 +3,15 @@
 Calls only the CPU oracle (``oracle/``) and the seeded input generators; no value
 here comes from the CUDA path.  Run from the repository root:
 
-    python tests/golden/make_golden.py [c2] [c3] [batch]
+    python tests/golden/make_golden.py [c2] [c3] [c3full] [batch]
 
 Outputs (text, one record per line):
   c2_segments.txt     l=20, n=8192, midpoint 1e15: per-segment composite counts,
                       plus the SHA-256 of the whole packed table.
   c3_samples.txt      l=20, n=32768, midpoint 2^60: 24 seeded segments, each with its
                       composite count and SHA-256.
+  c3_segments.txt     the same table whole: per-segment composite counts and the
+                      SHA-256 of all 2^35 bits (computed 512 segments at a time).
   batch_4096_seed0.txt  the 4096 seeded batch requests (j0, nbits) with each one's
                       composite count and SHA-256.
 Tables are hashed as little-endian uint32 words (bit j = word j/32, bit j%32).
@@ -67,6 +69,28 @@ def make_c3(nsamples=24):
     print("c3 %.0f s" % (time.time() - t0))
 
 
+def make_c3_full(chunk=512):
+    l, n = 20, 32768
+    f = oracle.f_from_midpoint(l, n, 1 << 60, 0)
+    base = oracle.base_for(2 * ((f + n) << l) - 1)
+    seg_words = (1 << l) // 32
+    h = hashlib.sha256()
+    counts = []
+    t0 = time.time()
+    for t0seg in range(0, n, chunk):
+        w = oracle.sieve(l, f + t0seg, chunk, base=base)
+        h.update(np.ascontiguousarray(w, dtype="<u4").tobytes())
+        counts += [oracle.popcount(w[k * seg_words:(k + 1) * seg_words]) for k in range(chunk)]
+        print("c3full %d/%d segments, %.0f s" % (t0seg + chunk, n, time.time() - t0), flush=True)
+    with open(os.path.join(HERE, "c3_segments.txt"), "w") as fh:
+        fh.write("# l=20 n=32768 midpoint=2^60 f=%d (written by tests/golden/make_golden.py "
+                 "from the CPU oracle, %.0f s)\n" % (f, time.time() - t0))
+        fh.write("# sha256 %s\n" % h.hexdigest())
+        fh.write("# total %d\n" % sum(counts))
+        for t, c in enumerate(counts):
+            fh.write("%d %d\n" % (t, c))
+
+
 _base = None
 
 
@@ -101,5 +125,5 @@ if __name__ == "__main__":
     which = sys.argv[1:] or ["c2", "c3", "batch"]
     for w in which:
         t = time.time()
-        {"c2": make_c2, "c3": make_c3, "batch": make_batch}[w]()
+        {"c2": make_c2, "c3": make_c3, "c3full": make_c3_full, "batch": make_batch}[w]()
         print(w, "done in %.0f s" % (time.time() - t), flush=True)
