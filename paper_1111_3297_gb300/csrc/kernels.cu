@@ -999,24 +999,29 @@ cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory atomic OR rate: every lane ORs into a random row of its own
-// bank (word = row*32 + lane), so a warp's 32 atomics never conflict
+// shared-memory atomic OR rate: a stream of conflict-free atomics with almost no
+// other instructions.  Lane k of a warp always addresses bank k (word row*32 + k),
+// and the rows are immediate offsets from one register, so the unrolled body is
+// one ATOMS per atomic and the loop adds two instructions per 64 atomics: the
+// kernel is bound by the shared-memory atomic unit, not by instruction issue.
 // ---------------------------------------------------------------------------
 constexpr int kProbeWords = 32768;  // 128 KB, the size of a 2^20-bit tile
-constexpr int kProbeIters = 4096;
+constexpr int kProbeUnroll = 64;    // atomics per loop trip (64 rows of 32 words)
+constexpr int kProbeTrips = 64;     // loop trips per thread
 
 __global__ void __launch_bounds__(1024) k_probe_smem(uint32_t *sink)
 {
     extern __shared__ uint32_t pm[];
     for (uint32_t i = threadIdx.x; i < kProbeWords; i += blockDim.x) pm[i] = 0;
     __syncthreads();
-    const uint32_t lane = threadIdx.x & 31;
-    uint32_t x = 0x9E3779B9u * (blockIdx.x * blockDim.x + threadIdx.x + 1);
-#pragma unroll 8
-    for (int it = 0; it < kProbeIters; ++it) {
-        x = x * 1664525u + 1013904223u;  // LCG (Numerical Recipes constants)
-        const uint32_t row = x >> 22;    // 0..1023
-        atomicOr(&pm[row * 32 + lane], 1u << (x & 31));
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp w works on rows 64*(w%16) .. +63 (a 32 KB-wide stripe per warp pair); bit
+    // values differ by thread so the table's final contents depend on every atomic
+    uint32_t *base = pm + (kProbeUnroll * 32) * (warp & 15) + lane;
+    const uint32_t bit = 1u << ((threadIdx.x * 7u + blockIdx.x) & 31);
+    for (int it = 0; it < kProbeTrips; ++it) {
+#pragma unroll
+        for (int k = 0; k < kProbeUnroll; ++k) atomicOr(base + 32 * k, bit);
     }
     __syncthreads();
     uint32_t v = 0;
@@ -1044,7 +1049,7 @@ cudaError_t probe_smem_atomics(int nsm, double *atom_per_s)
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
     if (e == cudaSuccess) e = cudaGetLastError();
-    *atom_per_s = (double)grid * 1024.0 * kProbeIters * reps / (ms * 1e-3);
+    *atom_per_s = (double)grid * 1024.0 * kProbeTrips * kProbeUnroll * reps / (ms * 1e-3);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);
