@@ -148,28 +148,48 @@ def test_config2_full_table_hash_and_segment_counts(ctx):
     assert S.sieve_count(ctx, out, n << l) == int(want_counts.sum())
 
 
-def test_config3_sampled_segments_and_miller_rabin(ctx):
+def test_config3_whole_table_segments_and_miller_rabin(ctx):
+    """The 2^60 configuration (l=20, n=32768) whole: SHA-256 of all 2^35 bits and every
+    segment's composite count against the oracle's stored values, the 24 stored
+    sampled segments, and 10^5 Miller-Rabin samples, half on 1 bits (composite) and
+    half on 0 bits (prime), drawn at seeded random positions."""
     l, n = 20, 32768
     f = oracle.f_from_midpoint(l, n, 1 << 60, 0)
     assert f == 2**39 - 16384
     out = torch.empty((n << l) // 32, dtype=torch.int32, device="cuda")
     S.sieve_segments(ctx, l, f, n, out)
     S.sieve_sync(ctx)
-    seg = out.view(n, (1 << l) // 32)
+    words = host_words(out)
+    del out
+    torch.cuda.empty_cache()
+    with open(os.path.join(GOLDEN, "c3_segments.txt")) as fh:
+        lines = fh.read().splitlines()
+    assert ("f=%d" % f) in lines[0]
+    want_sha = lines[1].split()[2]
+    want_counts = np.array([int(x.split()[1]) for x in lines[3:]], dtype=np.int64)
+    assert len(want_counts) == n
+    seg_words = (1 << l) // 32
+    seg = words.reshape(n, seg_words)
+    got_counts = np.array([oracle.popcount(seg[t]) for t in range(n)], dtype=np.int64)
+    bad = np.nonzero(got_counts != want_counts)[0]
+    assert len(bad) == 0, "segments with wrong counts: %s" % bad[:10]
+    assert sha(words) == want_sha
     with open(os.path.join(GOLDEN, "c3_samples.txt")) as fh:
         rows = [ln.split() for ln in fh if not ln.startswith("#")]
     for t, cnt, h in rows:
-        w = host_words(seg[int(t)])
-        assert oracle.popcount(w) == int(cnt), "segment %s" % t
-        assert sha(w) == h, "segment %s" % t
-    # random bits anywhere in the table against Miller-Rabin
-    rng = workloads.SplitMix64(33)
+        assert oracle.popcount(seg[int(t)]) == int(cnt), "segment %s" % t
+        assert sha(seg[int(t)]) == h, "segment %s" % t
+    # Miller-Rabin, stratified: 5e4 bits that are 1 and 5e4 that are 0
     J0 = f << l
-    for _ in range(3000):
-        j = rng.below(n << l)
-        word = int(out[j // 32].item()) & 0xFFFFFFFF
-        bit = (word >> (j % 32)) & 1
-        assert bit == (0 if oracle.is_prime_mr(2 * (J0 + j) + 1) else 1), j
+    rng = np.random.default_rng(0xC3)
+    pos = rng.integers(0, n << l, size=3_000_000, dtype=np.int64)
+    bits = (words[pos >> 5] >> (pos & 31).astype(np.uint32)) & 1
+    ones, zeros = pos[bits == 1][:50_000], pos[bits == 0][:50_000]
+    assert len(ones) == 50_000 and len(zeros) == 50_000
+    for j in ones.tolist():
+        assert not oracle.is_prime_mr(2 * (J0 + j) + 1), j
+    for j in zeros.tolist():
+        assert oracle.is_prime_mr(2 * (J0 + j) + 1), j
 
 
 def test_count_matches_numpy(ctx):
