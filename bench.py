@@ -48,6 +48,10 @@ def parse():
                     help="requests in the batched-vs-plain measurement (fewer for profiling cases)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-sweep-seconds", type=float, default=1.5,
+                    help="arrival time per rate of the saturating serving sweep (0: no sweep)")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 2^60 sub-record of the default run")
+    ap.add_argument("--fresh-steps", type=int, default=4, help="fresh-interval steps (0: none)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1e12..1e18 midpoint sweep")
     ap.add_argument("--clocks-csv", default="",
                     help="where to keep the nvidia-smi samples of the timed region (default: a temp file)")
@@ -132,11 +136,12 @@ def wheel_marks(J0, N, primes):
     ok = J1 <= Jlast
     c1 = (2 * J1 + 1) // p
     c2 = (2 * Jlast + 1) // p
-    R = np.array([1, 7, 11, 13, 17, 19, 23, 29])
+    # T[r] = residues in {1, 7, 11, 13, 17, 19, 23, 29} (odd, coprime to 15) that are <= r
+    T = np.cumsum(np.isin(np.arange(30), [1, 7, 11, 13, 17, 19, 23, 29]))
 
     def F(x):  # odd c <= x, coprime to 15
         q, r = np.divmod(x, 30)
-        return 8 * q + (R[None, :] <= r[:, None]).sum(axis=1)
+        return 8 * q + T[r]
 
     cnt = F(c2) - F(c1 - 1)
     return int(cnt[ok].sum())
@@ -145,15 +150,46 @@ def wheel_marks(J0, N, primes):
 PRESIEVE_MAX = [13, 23, 31, 41, 47, 59, 67, 73, 83, 97, 103, 109, 127]  # largest prime of groups 1..13
 
 
-def medium_marks(J0, N, tune):
+def medium_marks(J0, N, tune, primes=None):
     """Wheel-reduced marks of the primes the tile kernel strikes on [J0, J0+N): above
-    the pre-sieve's primes, up to medium_max and isqrt of the last number."""
-    import numpy as np
-    plimit = int(np.floor(np.sqrt(float(2 * (J0 + N) - 1))))
+    the pre-sieve's primes, up to medium_max and isqrt of the last number.  primes:
+    odd primes up to at least that bound (computed here when None)."""
+    import math
+    plimit = math.isqrt(2 * (J0 + N) - 1)
     top = min(plimit, tune["medium_max"])
-    primes = base_primes_upto(top)
-    medium = primes[(primes > PRESIEVE_MAX[tune["presieve_groups"] - 1]) & (primes <= top)]
-    return wheel_marks(J0, N, medium)
+    if primes is None:
+        primes = base_primes_upto(top)
+    import numpy as np
+    a = np.searchsorted(primes, PRESIEVE_MAX[tune["presieve_groups"] - 1], side="right")
+    b = np.searchsorted(primes, top, side="right")
+    return wheel_marks(J0, N, primes[a:b])
+
+
+def _marks_chunk(args):
+    reqs, tune = args
+    primes = base_primes_upto(tune["medium_max"])
+    return sum(medium_marks(j0, nb, tune, primes) for j0, nb in reqs)
+
+
+def batch_medium_marks(reqs, tune, world=1):
+    """Sum of medium_marks over many requests (j0, nbits), spread over this rank's share
+    of the host cores by a spawn-started process pool (never forked: the parent holds
+    a CUDA context); computed in this process if the pool fails or takes over 120 s."""
+    import multiprocessing as mp
+    k = max(1, min(16, (os.cpu_count() or 1) // max(1, world)))
+    chunks = [(reqs[i::k], tune) for i in range(k)]
+    if k > 1:
+        pool = None
+        try:
+            pool = mp.get_context("spawn").Pool(k)
+            return sum(pool.map_async(_marks_chunk, chunks).get(timeout=120))
+        except Exception:
+            pass
+        finally:
+            if pool is not None:
+                pool.terminate()
+                pool.join()
+    return sum(_marks_chunk(c) for c in chunks)
 
 
 def step_roofline(N, marks, h_large, visits, t_step, hbm_peak, r_atom):
@@ -291,13 +327,186 @@ def measure_sweep(S, ctx, hbm_peak, r_atom):
     return {"l": l, "n": n, "bits": N, "unit": "odd numbers/s", "points": points}
 
 
-def measure_batch(S, ctx, args, rank, world):
+def max_over_ranks(pg, x):
+    """Largest x over the ranks of the default process group (x itself without one):
+    the step time of a multi-rank run is the slowest rank's."""
+    if not pg:
+        return x
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, N, steps, ms_max):
+    """Whole-job throughput: the odd numbers all ranks sieved over the slowest rank's time."""
+    return world * N * steps / (ms_max * 1e-3)
+
+
+def load_traffic(key, N, h_large, n_tile, n_scatter):
+    """DRAM bytes per launch from the committed ncu capture of the same kernels on a
+    smaller slice of the same workload, scaled by the kernel's units per launch; None
+    when the kernels' code (kernels.cu, sieve_internal.cuh) changed since the capture."""
+    traffic = {"k_tile": None, "k_scatter": None}
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ksha = kernel_code_hash(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc"))
+        if key and tj.get("kernel_code_sha256_16") == ksha and key in tj:
+            tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
+            if n_tile:
+                traffic["k_tile"] = tt["dram_bytes"] / tt["units"] * (N / n_tile)
+            if n_scatter:
+                traffic["k_scatter"] = ts["dram_bytes"] / ts["units"] * (h_large / n_scatter)
+    except Exception:
+        pass
+    return traffic
+
+
+def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_atom, traffic_key,
+                     pg=None, clocks_path=""):
+    """One interval (l, f, n) sieved `steps` times into the same device table after
+    `warmup` untimed calls, CUDA events on the launching stream around the whole
+    timed region, nvidia-smi clocks sampled during it.  Returns the device-timed
+    figures with the per-kernel split, the dominant kernel's roofline and the step
+    roofline (the north-star definition), and keeps the table in ["out"]."""
+    import torch
+    N = n << l
+    J0 = f << l
+    stream = torch.cuda.current_stream()
+    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+    for _ in range(max(3, warmup)):
+        S.sieve_segments(ctx, l, f, n, out)
+    S.sieve_sync(ctx)
+
+    # ---- timed region: K steps, per-kernel CUDA events inside the library ----
+    S.sieve_profile_enable(ctx, True)
+    S.sieve_profile_read(ctx)  # reset
+    clocks = Clocks(torch.cuda.current_device(), clocks_path)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        S.sieve_segments(ctx, l, f, n, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = S.sieve_profile_read(ctx)
+    S.sieve_profile_enable(ctx, False)
+    S.sieve_sync(ctx)
+    # one more step (not timed) with the scatter and tile launches on one stream: each
+    # kernel's own time, whose shares compare with the ncu launch list and which picks
+    # the dominant kernel (inside the timed region the two overlap and share the SMs)
+    S.sieve_profile_enable(ctx, True, serial=True)
+    S.sieve_profile_read(ctx)
+    S.sieve_segments(ctx, l, f, n, out)
+    prof_serial = S.sieve_profile_read(ctx)
+    S.sieve_profile_enable(ctx, False)
+    S.sieve_sync(ctx)
+    ms_max = max_over_ranks(pg, ms)
+
+    h_medium = medium_marks(J0, N, tune)  # per step
+    h_large = prof["large_hits"] / steps
+    visits = prof["prime_reads"] / steps
+    t_tile = prof["ms"][S.K_TILE] / steps * 1e-3
+    t_scatter = prof["ms"][S.K_SCATTER] / steps * 1e-3
+    n_tile = prof["launches"][S.K_TILE] / steps
+    n_scatter = prof["launches"][S.K_SCATTER] / steps
+    marks = h_medium + h_large
+    # tile: table written once, each bucket entry read once; scatter (one interval):
+    # each bucket entry written once, and per prime and scatter group the prime (4 B)
+    # and its 8-byte state word read and written back
+    tile_bytes = N / 8 + 4 * h_large
+    scatter_bytes = 4 * h_large + 20 * visits
+    kernels = {
+        "k_tile": {"ms_per_step": t_tile * 1e3, "launches_per_step": n_tile,
+                   "marks": marks, "atomics_per_s": marks / t_tile if t_tile else None,
+                   "hbm_bytes": tile_bytes, "hbm_gbs": tile_bytes / t_tile / 1e9 if t_tile else None},
+        "k_scatter": {"ms_per_step": t_scatter * 1e3, "launches_per_step": n_scatter,
+                      "hits": h_large, "visits": visits, "hbm_bytes": scatter_bytes,
+                      "hbm_gbs": scatter_bytes / t_scatter / 1e9 if t_scatter else None},
+    }
+    traffic = load_traffic(traffic_key, N, h_large, n_tile, n_scatter)
+    st_tile, st_scatter = prof_serial["ms"][S.K_TILE], prof_serial["ms"][S.K_SCATTER]
+    kernels["serialised_step"] = {
+        "k_tile_ms": st_tile, "k_scatter_ms": st_scatter,
+        "k_tile_share": st_tile / (st_tile + st_scatter) if st_tile + st_scatter else None,
+        "k_scatter_share": st_scatter / (st_tile + st_scatter) if st_tile + st_scatter else None}
+    if st_tile >= st_scatter:
+        ach = marks / t_tile / 1e9
+        roof = {"kernel": "k_tile", "bound": "smem_atomic", "achieved": ach, "peak": r_atom / 1e9,
+                "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": traffic["k_tile"],
+                "peak_source": "measured in this run (conflict-free shared atomicOr stream, "
+                               "bound by the atomic unit)",
+                "hbm_achieved_gbs": tile_bytes / t_tile / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": tile_bytes / t_tile / 1e9 / hbm_peak}
+    else:
+        ach = scatter_bytes / t_scatter / 1e9
+        roof = {"kernel": "k_scatter", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic["k_scatter"],
+                "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    step_roof = step_roofline(N, marks, h_large, visits, ms_max * 1e-3 / steps, hbm_peak, r_atom)
+    # beside the north-star figure (16 B per hit: the paper's (p, q) pair written and
+    # read), the bytes this design moves: 4-byte bucket entries written and read
+    b_impl = N / 8 + 8 * h_large + 20 * visits
+    step_roof["bytes_impl"] = b_impl
+    step_roof["t_hbm_impl_ms"] = b_impl / (hbm_peak * 1e9) * 1e3
+    return {"N": N, "ms": ms_max, "steps": steps, "value_local": N * steps / (ms * 1e-3),
+            "ms_max": ms_max, "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+            "clocks": clk, "launches": int(sum(prof["launches"])), "out": out}
+
+
+def measure_fresh(S, ctx, l, f, n, steps, host=False):
+    """Throughput over fresh intervals: step k sieves (l, f + (k+1) n, n), so every
+    step builds its plan (tiles, scatter groups, chunks), uploads its descriptors and
+    runs it uncaptured -- the first-call cost of a new interval.  Device figure: CUDA
+    events around all steps (host planning stalls the stream, so it is inside);
+    host=True: the table goes to pinned host memory (sieve_segments_host) and the
+    figure is wall-clock time."""
+    import torch
+    N = n << l
+    if host:
+        buf = torch.empty(N // 32, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            S.sieve_segments_host(ctx, l, f + (k + 1) * n, n, buf)
+        dt = time.perf_counter() - t0
+        del buf
+        return {"value": N * steps / dt, "ms_per_step": dt / steps * 1e3, "steps": steps}
+    stream = torch.cuda.current_stream()
+    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(steps):
+        S.sieve_segments(ctx, l, f + (k + 1) * n, n, out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.sieve_sync(ctx)
+    ms = ev0.elapsed_time(ev1)
+    del out
+    return {"value": N * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps}
+
+
+def measure_batch(S, ctx, args, rank, world, hbm_peak, r_atom):
     """args.batch_requests (4096) seeded requests of uneven length (2^16..2^28 numbers) and magnitude
     (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
-    plain form (one sieve_segments call per request), same outputs, same GPU."""
+    plain form (one sieve_segments call per request), same outputs (every request's
+    count compared), same GPU, with the batched form's step roofline.  Under torchrun
+    each rank takes its share of one seeded request list (shard.partition_requests)."""
+    import numpy as np
     import torch
-    from paper_1111_3297_gb300 import workloads
-    reqs = workloads.batch_requests(args.batch_requests, seed=rank)
+    from paper_1111_3297_gb300 import shard, workloads
+    allreqs = workloads.batch_requests(args.batch_requests, seed=0)
+    mine = shard.partition_requests(allreqs, rank, world)
+    reqs = [allreqs[i] for i in mine]
     lay, off = [], 0
     for j0, nb in reqs:
         lay.append((j0, nb, off))
@@ -322,6 +531,13 @@ def measure_batch(S, ctx, args, rank, world):
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) * 1e-3 / ksteps
     ref = counts.cpu().clone()
+    # one more (untimed) call with profiling on: exact large-prime hits and visits
+    S.sieve_profile_enable(ctx, True)
+    S.sieve_profile_read(ctx)
+    S.sieve_batch(ctx, lay, arena, counts)
+    prof = S.sieve_profile_read(ctx)
+    S.sieve_profile_enable(ctx, False)
+    S.sieve_sync(ctx)
     # plain: one call per request into the same arena slots
     for j0, nb, o in lay:
         S.sieve_segments(ctx, 5, j0 // 32, nb // 32, arena[o:o + nb // 32])
@@ -334,26 +550,37 @@ def measure_batch(S, ctx, args, rank, world):
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) * 1e-3
     same = all(S.sieve_count(ctx, arena[o:o + nb // 32], nb) == int(c)
-               for (j0, nb, o), c in zip(lay[:256], ref.tolist()[:256]))
+               for (j0, nb, o), c in zip(lay, ref.tolist()))
+    # roofline of the batched form: per request its wheel-reduced medium marks, plus the
+    # large-prime hits and (prime, unit) first-hit visits the library counted
+    vmax = max(2 * (j0 + nb - 1) + 1 for j0, nb in reqs)
+    tune = tuned or S.sieve_get_tuning(ctx, 0 if vmax < 2**40 else 1 if vmax < 2**50 else 2 if vmax < 2**56 else 3)
+    h_med = batch_medium_marks(reqs, {"medium_max": tune["medium_max"], "presieve_groups": tune["presieve_groups"]},
+                               world)
+    h_large, visits = prof["large_hits"], prof["prime_reads"]
+    roof = step_roofline(bits, h_med + h_large, h_large, visits, t_batch, hbm_peak, r_atom)
+    roof["first_hit_visits_per_s"] = visits / t_batch
+    roof["note"] = ("the multi-request scatter is bound by its (prime, unit) first-hit visits: "
+                    "Barrett reduction and wheel start per visit, issue-bound (see DESIGN)")
     del arena, counts
     torch.cuda.empty_cache()
-    return {"requests": len(reqs), "odd_numbers": bits, "batched": bits / t_batch, "plain": bits / t_plain,
+    return {"requests": len(reqs), "requests_all_ranks": len(allreqs), "odd_numbers": bits,
+            "batched": bits / t_batch, "plain": bits / t_plain,
             "unit": "odd numbers/s", "speedup": t_plain / t_batch, "batched_ms": t_batch * 1e3,
-            "plain_ms": t_plain * 1e3, "same_counts_first256": same, "tuning": tuned,
-            "autotune_s": t_tune}
+            "plain_ms": t_plain * 1e3, "same_counts_all": same, "tuning": tuned,
+            "autotune_s": t_tune, "roofline": roof}
 
 
-def measure_serving(S, ctx, args, rank):
-    """Seeded Poisson arrivals (2000 requests/s) of requests drawn as in the batch,
-    admission capped by 64 GB of device memory; p50/p99 latency (submit -> done)
-    and sustained odd numbers/s."""
+def serve_at(S, ctx, rate, count, rank, seed=0):
+    """Seeded Poisson arrivals at `rate` requests/s of `count` requests drawn as in the
+    batch, admission capped by 64 GB of device memory; latency (submit -> done) and
+    sustained odd numbers/s, and the requests in the system (submitted, not yet done)."""
     from paper_1111_3297_gb300 import workloads
-    rate = 2000.0
-    count = int(rate * args.serve_seconds)
-    reqs = workloads.batch_requests(count, seed=100 + rank)
-    arrivals = workloads.poisson_arrivals(count, rate, seed=rank)
+    reqs = workloads.batch_requests(count, seed=100 + seed + rank)
+    arrivals = workloads.poisson_arrivals(count, rate, seed=seed + rank)
     srv = S.Server(ctx, mem_cap=64 << 30, max_inflight=4)
     lat, done_bits, first, last = [], 0, None, 0.0
+    depth_max, depth_sum, depth_n = 0, 0, 0
     try:
         i = 0
         t_start = srv.now()
@@ -364,6 +591,9 @@ def measure_serving(S, ctx, args, rank):
                 srv.submit(*reqs[i])
                 pending += 1
                 i += 1
+            depth_max = max(depth_max, pending)
+            depth_sum += pending
+            depth_n += 1
             for r in srv.poll(1024, timeout_ms=0 if i < count else 50):
                 if r["status"] != 0:
                     raise RuntimeError("served request failed with status %d" % r["status"])
@@ -383,7 +613,23 @@ def measure_serving(S, ctx, args, rank):
     q = lambda x: lat[min(len(lat) - 1, int(x * len(lat)))]  # noqa: E731
     return {"requests": count, "rate_per_s": rate, "p50_ms": q(0.50) * 1e3, "p99_ms": q(0.99) * 1e3,
             "max_ms": lat[-1] * 1e3, "sustained": done_bits / (last - first), "unit": "odd numbers/s",
-            "offered": sum(nb for _, nb in reqs) / arrivals[-1], "mem_cap_gb": 64, "lanes": 4}
+            "offered": sum(nb for _, nb in reqs) / arrivals[-1], "in_system_max": depth_max,
+            "in_system_mean": depth_sum / max(1, depth_n), "mem_cap_gb": 64, "lanes": 4}
+
+
+def measure_serving(S, ctx, args, rank):
+    """The serving configuration (2000 requests/s for args.serve_seconds), then a
+    saturating sweep of arrival rates up to past the server's capacity, each rate for
+    a few seconds of arrivals."""
+    main = serve_at(S, ctx, 2000.0, int(2000.0 * args.serve_seconds), rank)
+    sweep = []
+    if args.serve_sweep_seconds > 0:
+        for rate in (2000.0, 8000.0, 20000.0, 50000.0, 120000.0):
+            r = serve_at(S, ctx, rate, int(rate * args.serve_sweep_seconds), rank, seed=7)
+            sweep.append({k: r[k] for k in ("rate_per_s", "requests", "p50_ms", "p99_ms", "sustained", "offered",
+                                            "in_system_max", "in_system_mean")})
+    main["sweep"] = sweep
+    return main
 
 
 def main():
@@ -417,13 +663,12 @@ def main():
         f0 = S.sieve_f_from_midpoint(l, n, wl["mant"], wl["exp10"])
     f, _ = shard.shard(l, f0, n, rank, world, "weak")  # each rank its own n segments
     N = n << l
-    J0 = f << l
     vmax = 2 * ((f0 + world * n) << l)
-    # the batch and serving legs draw requests up to ~1e18
-    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 31))
-                       if not (args.no_batch and args.no_serve and args.no_sweep) else vmax)
-    stream = torch.cuda.current_stream()
-    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+    c3_on = args.workload == "c2" and not args.no_c3 and not args.segments
+    # the batch and serving legs draw requests up to ~1e18, the 2^60 sub-record sieves
+    # up to 2^60 + 2^35
+    wide = not (args.no_batch and args.no_serve and args.no_sweep) or c3_on
+    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 31)) if wide else vmax)
 
     tuned = None
     if args.tuning:
@@ -433,49 +678,25 @@ def main():
     elif not args.no_autotune:
         tuned = S.sieve_autotune(ctx, l, f, n)
     r_atom = S.sieve_probe_smem_atomics(local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cls = 0 if vmax < 2**40 else 1 if vmax < 2**50 else 2 if vmax < 2**56 else 3
+    tune = tuned or S.sieve_get_tuning(ctx, cls)
 
-    for _ in range(max(3, args.warmup)):
-        S.sieve_segments(ctx, l, f, n, out)
-    S.sieve_sync(ctx)
-
-    # ---- timed region: K steps, per-kernel CUDA events inside the library ----
-    S.sieve_profile_enable(ctx, True)
-    S.sieve_profile_read(ctx)  # reset
-    clocks = Clocks(local, args.clocks_csv)
-    clocks.start()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        S.sieve_segments(ctx, l, f, n, out)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    prof = S.sieve_profile_read(ctx)
-    S.sieve_profile_enable(ctx, False)
-    S.sieve_sync(ctx)
-    ms_max = ms
-    # one more step (not timed) with the scatter and tile launches on one stream: each
-    # kernel's own time, whose shares compare with the ncu launch list and which picks
-    # the dominant kernel (inside the timed region the two overlap and share the SMs)
-    S.sieve_profile_enable(ctx, True, serial=True)
-    S.sieve_profile_read(ctx)
-    S.sieve_segments(ctx, l, f, n, out)
-    prof_serial = S.sieve_profile_read(ctx)
-    S.sieve_profile_enable(ctx, False)
-    S.sieve_sync(ctx)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max * 1e-3)
-
+    m = measure_interval(S, ctx, l, f, n, args.steps, args.warmup, tune, hbm_peak, hbm_src, r_atom,
+                         {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload), pg,
+                         args.clocks_csv)
+    out = m.pop("out")
+    ms_max = m["ms_max"]
+    value = job_value(world, N, args.steps, ms_max)
     composites = shard.total_count(S.sieve_count(ctx, out, N))
+    del out
+    torch.cuda.empty_cache()
 
     # ---- end to end: the table delivered to pinned host memory ----
     e2e = None
@@ -488,85 +709,41 @@ def main():
         ksteps = max(1, min(args.steps, 5))
         for _ in range(ksteps):
             S.sieve_segments_host(ctx, l, f, n, host)
-        dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * N * ksteps / dt, "unit": "odd numbers/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": N // 8, "steps": ksteps}
+        dt = max_over_ranks(pg, time.perf_counter() - t0)
+        # inputs are the call's three scalars (l, f, n); the plan's descriptors were
+        # uploaded by the warm-up call and stay cached with its graph
+        e2e = {"value": world * N * ksteps / dt, "unit": "odd numbers/s", "h2d_bytes_per_step": 24,
+               "d2h_bytes_per_step": N // 8, "steps": ksteps,
+               "inputs": "three 8-byte scalars (l, f, n) passed by value; plan descriptors cached"}
         del host
 
-    # ---- roofline of the dominant kernel ----
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    tune = S.sieve_get_tuning(ctx, 0 if vmax < 2**40 else 1 if vmax < 2**50 else 2 if vmax < 2**56 else 3)
-    if tuned:
-        tune = tuned
-    h_medium = medium_marks(J0, N, tune)  # per step
-    steps = args.steps
-    h_large = prof["large_hits"] / steps
-    t_tile = prof["ms"][S.K_TILE] / steps * 1e-3
-    t_scatter = prof["ms"][S.K_SCATTER] / steps * 1e-3
-    n_tile = prof["launches"][S.K_TILE] / steps
-    n_scatter = prof["launches"][S.K_SCATTER] / steps
-    marks = h_medium + h_large
-    # tile: table written once, each bucket entry read once; scatter (one interval):
-    # each bucket entry written once, and per prime and scatter group the prime (4 B)
-    # and its 8-byte state word read and written back
-    tile_bytes = N / 8 + 4 * h_large
-    scatter_bytes = 4 * h_large + 20 * prof["prime_reads"] / steps
-    kernels = {
-        "k_tile": {"ms_per_step": t_tile * 1e3, "launches_per_step": n_tile,
-                   "marks": marks, "atomics_per_s": marks / t_tile if t_tile else None,
-                   "hbm_bytes": tile_bytes, "hbm_gbs": tile_bytes / t_tile / 1e9 if t_tile else None},
-        "k_scatter": {"ms_per_step": t_scatter * 1e3, "launches_per_step": n_scatter,
-                      "hits": h_large, "hbm_bytes": scatter_bytes,
-                      "hbm_gbs": scatter_bytes / t_scatter / 1e9 if t_scatter else None},
-    }
-    # DRAM traffic per launch from the committed ncu capture of the same kernel on a
-    # smaller slice of the same workload, scaled by the kernel's units per launch;
-    # null when the kernels' code (kernels.cu, sieve_internal.cuh) changed since the capture
-    traffic = {"k_tile": None, "k_scatter": None}
-    try:
-        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ksha = kernel_code_hash(os.path.join(ROOT, "paper_1111_3297_gb300", "csrc"))
-        key = {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload)
-        if key and tj.get("kernel_code_sha256_16") == ksha and key in tj:
-            tt, ts = tj[key]["k_tile"], tj[key]["k_scatter"]
-            if n_tile:
-                traffic["k_tile"] = tt["dram_bytes"] / tt["units"] * (N / n_tile)
-            if n_scatter:
-                traffic["k_scatter"] = ts["dram_bytes"] / ts["units"] * (h_large / n_scatter)
-    except Exception:
-        pass
-    # the dominant kernel: the larger share of the step when the two run one after
-    # the other (the serialised step above)
-    st_tile, st_scatter = prof_serial["ms"][S.K_TILE], prof_serial["ms"][S.K_SCATTER]
-    kernels["serialised_step"] = {
-        "k_tile_ms": st_tile, "k_scatter_ms": st_scatter,
-        "k_tile_share": st_tile / (st_tile + st_scatter) if st_tile + st_scatter else None,
-        "k_scatter_share": st_scatter / (st_tile + st_scatter) if st_tile + st_scatter else None}
-    if st_tile >= st_scatter:
-        ach = marks / t_tile / 1e9
-        roof = {"kernel": "k_tile", "bound": "smem_atomic", "achieved": ach, "peak": r_atom / 1e9,
-                "unit": "Gatomic/s", "frac": ach / (r_atom / 1e9), "traffic": traffic["k_tile"],
-                "peak_source": "measured in this run (conflict-free shared atomicOr probe)",
-                "hbm_achieved_gbs": tile_bytes / t_tile / 1e9, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": tile_bytes / t_tile / 1e9 / hbm_peak}
-    else:
-        ach = scatter_bytes / t_scatter / 1e9
-        roof = {"kernel": "k_scatter", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": traffic["k_scatter"],
-                "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
-    # step-level roofline: the slower of HBM bytes at peak and marks at the atomic peak
-    step_roof = step_roofline(N, marks, h_large, prof["prime_reads"] / steps, ms_max * 1e-3 / steps,
-                              hbm_peak, r_atom)
+    # ---- fresh intervals: plan building, descriptor upload inside every step ----
+    fresh = None
+    if args.fresh_steps > 0 and rank == 0:
+        fresh = {"device": measure_fresh(S, ctx, l, f, n, args.fresh_steps),
+                 "e2e": measure_fresh(S, ctx, l, f + args.fresh_steps * n, n, args.fresh_steps, host=True),
+                 "note": "step k sieves (l, f + (k+1) n, n): every step a new interval, its plan built, "
+                         "uploaded and run uncaptured"}
+
+    # ---- the 2^60 configuration (l = 20, n = 32768) as a sub-record ----
+    c3 = None
+    if c3_on and rank == 0:
+        w3 = WORKLOADS["c3"]
+        f3 = S.sieve_f_from_midpoint(w3["l"], w3["n"], w3["mant"], w3["exp10"])
+        t3 = S.sieve_get_tuning(ctx, 3)
+        k3 = min(args.steps, 5)
+        m3 = measure_interval(S, ctx, w3["l"], f3, w3["n"], k3, 3, t3, hbm_peak, hbm_src, r_atom,
+                              "l20_n4096_mid2p60")
+        out3 = m3.pop("out")
+        m3["composites"] = S.sieve_count(ctx, out3, m3["N"])
+        del out3
+        torch.cuda.empty_cache()
+        c3 = {"config": {"workload": w3["name"], "l": w3["l"], "f": f3, "n": w3["n"], "tuning": t3,
+                         "l2": "table 4096 MiB + buckets, larger than L2"},
+              "value": m3["value_local"], "unit": "odd numbers/s", "ms_per_step": m3["ms"] / k3,
+              "steps": k3, "warmup": 3, **{k: m3[k] for k in ("roofline", "step_roofline", "kernels",
+                                                             "clocks", "composites")}}
+
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = measure_sweep(S, ctx, hbm_peak, r_atom)
@@ -574,11 +751,9 @@ def main():
     base_line = None
     if rank == 0 and not args.no_cpu_baseline:
         base_line = cpu_baseline(dict(wl, n=n), f0)
-    del out
-    torch.cuda.empty_cache()
     batch = None
     if not args.no_batch:
-        batch = measure_batch(S, ctx, args, rank, world)
+        batch = measure_batch(S, ctx, args, rank, world, hbm_peak, r_atom)
     serving = None
     if not args.no_serve:
         serving = measure_serving(S, ctx, args, rank)
@@ -592,10 +767,10 @@ def main():
             "config": {"workload": wl["name"], "l": l, "f": f0, "n": n, "parallelism": "interval shards x%d" % world,
                        "l2": "working set larger than L2 (table %d MiB + buckets)" % (N // 8 // 2**20),
                        "tuning": tune},
-            "gpu_launches": int(sum(prof["launches"])),
-            "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
-            "cpu_baseline": base_line, "e2e": e2e, "clocks": clk,
-            "batch": batch, "serving": serving, "sweep": sweep,
+            "gpu_launches": m["launches"],
+            "roofline": m["roofline"], "step_roofline": m["step_roofline"], "kernels": m["kernels"],
+            "cpu_baseline": base_line, "e2e": e2e, "fresh": fresh, "clocks": m["clocks"],
+            "c3": c3, "batch": batch, "serving": serving, "sweep": sweep,
             "composites": composites, "smem_atomic_peak_per_s": r_atom,
         }), flush=True)
     ctx.close()
