@@ -45,6 +45,9 @@ def _load():
         lib.oracle_is_composite_trial.argtypes = [_u64]
         lib.oracle_is_prime_mr.restype = ctypes.c_int
         lib.oracle_is_prime_mr.argtypes = [_u64]
+        lib.oracle_segment_counts.restype = ctypes.c_int
+        lib.oracle_segment_counts.argtypes = [ctypes.c_void_p, _u64, _u64, _u32, ctypes.c_void_p,
+                                              ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -141,6 +144,22 @@ def is_composite_trial(m: int) -> bool:
 
 def is_prime_mr(m: int) -> bool:
     return bool(_load().oracle_is_prime_mr(m))
+
+
+def segment_counts(words: np.ndarray, J0: int, nbits: int, l: int):
+    """(primes, twins) per segment of 2^l bits of a table whose bit j stands for
+    2(J0 + j) + 1: the primes (0 bits, the number 1 excluded) and the twin pairs
+    (m, m + 2) both prime with m + 2 inside the first nbits bits, by the segment of m
+    (oracle_segment_counts)."""
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    assert 32 * len(words) >= nbits
+    nseg = (nbits + (1 << l) - 1) >> l
+    pr = np.zeros(max(nseg, 1), dtype=np.uint64)
+    tw = np.zeros(max(nseg, 1), dtype=np.uint64)
+    rc = _load().oracle_segment_counts(words.ctypes.data, J0, nbits, l, pr.ctypes.data, tw.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_segment_counts failed with code %d" % rc)
+    return pr[:nseg].astype(np.int64), tw[:nseg].astype(np.int64)
 
 
 def get_bit(words: np.ndarray, j: int) -> int:

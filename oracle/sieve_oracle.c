@@ -286,3 +286,27 @@ int oracle_get_bit(const uint32_t *words, uint64_t j)
 {
     return (int)((words[j / 32] >> (j % 32)) & 1u);
 }
+
+/* Consumers of a finished table (Sec. 5: the table is made to be used, e.g. for
+ * prime counts and the Goldbach search): per segment of 2^l bits, the primes and
+ * the twin pairs.  Bit j (0 <= j < nbits) of `words` stands for m = 2(J0 + j) + 1;
+ * m is a prime when the bit is 0 and m != 1 (the table's 0 bits are exactly the
+ * primes and the number 1).  A twin pair is (m, m + 2) with both prime; m + 2 is
+ * bit j + 1, so the pair is counted only when j + 1 < nbits, in the segment j >> l
+ * of its lower member.  Plain loop over bits; primes[] and twins[] hold
+ * ceil(nbits / 2^l) entries and are overwritten. */
+int oracle_segment_counts(const uint32_t *words, uint64_t J0, uint64_t nbits, uint32_t l,
+                          uint64_t *primes, uint64_t *twins)
+{
+    if (l > 62 || (nbits && !words)) return ORACLE_EINVAL;
+    const uint64_t nseg = (nbits + ((uint64_t)1 << l) - 1) >> l;
+    for (uint64_t t = 0; t < nseg; ++t) primes[t] = twins[t] = 0;
+    int prev_prime = 0; /* bit j - 1 is a prime */
+    for (uint64_t j = 0; j < nbits; ++j) {
+        const int is_prime = oracle_get_bit(words, j) == 0 && J0 + j != 0;
+        if (is_prime) primes[j >> l]++;
+        if (is_prime && prev_prime) twins[(j - 1) >> l]++;
+        prev_prime = is_prime;
+    }
+    return ORACLE_OK;
+}
