@@ -94,6 +94,24 @@ sieve_status sieve_segments_midpoint(sieve_ctx *ctx, uint32_t l, uint64_t mant, 
                                      uint64_t n, uint32_t *dev_bits, sieve_stream stream);
 
 /*
+ * Prime and twin-prime counts per segment, without writing the table: a consumer of
+ * the sieve table fused into the segment kernel (Sec. 5 names such uses of the table;
+ * Definition "Sieve table, Segments", Sec. 1.3, fixes the segments).  Sieves the same
+ * interval as sieve_segments(l, f, n) and, for each segment t < n (the 2^l odd numbers
+ * m = 2(f*2^l + t*2^l + j) + 1, 0 <= j < 2^l), writes to caller-owned device memory
+ *   dev_primes[t]  the number of primes m in segment t (1 is not a prime);
+ *   dev_twins[t]   the number of twin pairs (m, m + 2), both prime, with m in segment t
+ *                  and m + 2 inside the interval (NULL: not counted).
+ * Both arrays are uint64_t[n], 8-byte aligned; they are overwritten (not accumulated),
+ * asynchronously on `stream`.  The sum of dev_primes is the interval's prime count.
+ * Requires 12 <= l <= 40 (segments of at least 4096 bits); otherwise as sieve_segments
+ * (SIEVE_EINVAL, SIEVE_ERANGE; device errors at the next waiting call).  The call keeps
+ * a plan per (interval, output pointers), like sieve_segments.
+ */
+sieve_status sieve_count_segments(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64_t n,
+                                  uint64_t *dev_primes, uint64_t *dev_twins, sieve_stream stream);
+
+/*
  * End-to-end form of sieve_segments: the table lands in caller-owned HOST memory
  * host_bits (n*2^(l-5) words; pinned memory copies fastest).  The context sieves
  * it in epochs of at most 2^30 bits into a two-slot device ring and copies each

@@ -585,6 +585,7 @@ Plan::~Plan()
     if (d_sus) cudaFree(d_sus);
     if (d_groups) cudaFree(d_groups);
     if (d_chunks) cudaFree(d_chunks);
+    if (d_edge) cudaFree(d_edge);
 }
 
 template <class T>
@@ -639,6 +640,10 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
     CK(cudaStreamWaitEvent(ss, scr.ev_fork, 0));
     if (counts && ncounts) CK(cudaMemsetAsync(counts, 0, (size_t)ncounts * 8, st));
+    if (P->count_mode) {
+        CK(cudaMemsetAsync(P->seg_primes, 0, (size_t)P->nsegs * 8, st));
+        if (P->seg_twins) CK(cudaMemsetAsync(P->seg_twins, 0, (size_t)P->nsegs * 8, st));
+    }
     bool run_first = true;
     for (size_t ei = 0; ei < P->epochs.size(); ++ei) {
         const Plan::Epoch &e = P->epochs[ei];
@@ -702,6 +707,11 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         ta.run = 0;
         ta.carry_h = scr.d_tcarry_h;
         ta.carry_stride = P->lane_stride;
+        ta.seg_primes = P->count_mode ? P->seg_primes : nullptr;
+        ta.seg_twins = P->count_mode ? P->seg_twins : nullptr;
+        ta.edge = P->count_mode ? P->d_edge + e.tile0 : nullptr;
+        ta.seg_j0 = P->seg_j0;
+        ta.seg_l = P->seg_l;
         if (P->single_request && scr.d_tcarry_h && P->lane_stride && P->tune.medium_max <= (1u << 26)) {
             // one request: contiguous runs of tiles per CTA, carrying next hits (offsets
             // below 3 * medium_max <= 2^28 and run spans below 2^29 - 1 bits)
@@ -724,6 +734,9 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
         }
     }
+    // count mode: the twin pairs that straddle two tiles, once every tile is done
+    if (P->count_mode && P->seg_twins)
+        CK(launch_seg_edges(P->d_tiles, P->d_edge, (uint32_t)P->tiles.size(), P->seg_j0, P->seg_l, P->seg_twins, st));
     CK(cudaEventRecord(scr.ev_join, ss));
     CK(cudaStreamWaitEvent(st, scr.ev_join, 0));
     CK(cudaEventRecord(scr.ev_join, st));
@@ -1068,6 +1081,42 @@ try {
     Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
     if (!P) return SIEVE_ERANGE;
     return run_plan(c, P, dev_bits, nullptr, (cudaStream_t)stream, true);
+} catch (...) {
+    return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
+}
+
+sieve_status sieve_count_segments(sieve_ctx *c, uint32_t l, uint64_t f, uint64_t n, uint64_t *dev_primes,
+                                  uint64_t *dev_twins, sieve_stream stream)
+try {
+    if (!c || !dev_primes || l < 12 || l > 40 || n == 0 || ((uintptr_t)dev_primes & 7) ||
+        ((uintptr_t)dev_twins & 7))
+        return SIEVE_EINVAL;
+    if ((((unsigned __int128)f + n) << l) > ((unsigned __int128)1 << 63)) return SIEVE_ERANGE;
+    const uint64_t j0 = f << l, nbits = n << l;
+    uint64_t vlast;
+    sieve_status s = check_range(c, j0, nbits, &vlast);
+    if (s) return s;
+    CK(cudaSetDevice(c->device));
+    // tiles of >= 2^12 bits (tuning ranges) start 2^12-aligned relative to j0 and, since
+    // 2^l >= 2^12 divides nbits, every tile is whole 4096-bit chunks of one segment
+    const sieve_tuning t = tuning_for(c, vlast, nbits);
+    char key[200];
+    std::snprintf(key, sizeof key, "C/%llu/%llu/%u/%p/%p/", (unsigned long long)j0, (unsigned long long)nbits, l,
+                  (void *)dev_primes, (void *)dev_twins);
+    std::vector<ReqSpec> reqs{{j0, nbits, 0, 0}};
+    Plan *P = cached_plan(c, std::string(key) + tune_key(t), reqs, t);
+    if (!P) return SIEVE_ERANGE;
+    if (!P->count_mode) {
+        s = alloc_dev((void **)&P->d_edge, P->tiles.size());
+        if (s) return s;
+        P->count_mode = true;
+        P->seg_primes = reinterpret_cast<unsigned long long *>(dev_primes);
+        P->seg_twins = reinterpret_cast<unsigned long long *>(dev_twins);
+        P->seg_j0 = j0;
+        P->seg_l = l;
+        P->nsegs = n;
+    }
+    return run_plan(c, P, nullptr, nullptr, (cudaStream_t)stream, true);
 } catch (...) {
     return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
 }

@@ -60,6 +60,12 @@ struct Plan {
     uint32_t lane_stride = 0;    // one-prime-per-thread primes of the widest tile
     uint64_t bits = 0;
     double exp_large_hits = 0;
+    // count mode (sieve_count_segments): no table; per-segment prime and twin counts
+    bool count_mode = false;
+    unsigned long long *seg_primes = nullptr, *seg_twins = nullptr;  // caller's device counters
+    uint64_t seg_j0 = 0, nsegs = 0;
+    uint32_t seg_l = 0;
+    uint8_t *d_edge = nullptr;   // per tile: first / last bit is a prime
     // device copies of the descriptors
     TileDesc *d_tiles = nullptr;
     SUDesc *d_sus = nullptr;

@@ -117,13 +117,88 @@ __device__ __forceinline__ void presieve_pass(uint32_t *sm, const TileArgs &a, c
         sm[w] = mask;
     }
 }
+// Count mode of the finished tile in shared memory (Sec. 5: the table consumed where it
+// is made).  A zero bit j is a prime 2(J+j)+1, except the number 1; a twin pair is two
+// adjacent zero bits (the odd numbers m and m+2).  The host guarantees 2^seg_l >= 4096
+// and tiles of whole 4096-bit chunks starting 4096-aligned relative to seg_j0, so the
+// 32 uint4 words a warp reads in one trip lie in one segment.  The pair formed by the
+// tile's last bit and the next tile's first bit is left to k_seg_edges.
+template <int T>
+__device__ __forceinline__ void tile_counts(const uint32_t *sm, const TileArgs &a, const TileDesc &d,
+                                            uint32_t t, uint32_t nwords, uint32_t *s_red)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n4 = nwords >> 2;  // a multiple of 32
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sm);
+    const bool per_chunk = a.seg_l < a.tile_log2;  // several segments per tile
+    uint32_t tp = 0, tt = 0;
+    for (uint32_t i = tid; i < n4; i += T) {
+        const uint4 v = s4[i];
+        const uint32_t z0 = ~v.x, z1 = ~v.y, z2 = ~v.z, z3 = ~v.w;
+        const uint32_t z4 = 4 * i + 4 < nwords ? ~sm[4 * i + 4] : 0u;  // past the tile: left to k_seg_edges
+        uint32_t pc = __popc(z0) + __popc(z1) + __popc(z2) + __popc(z3);
+        uint32_t tc = __popc(z0 & ((z0 >> 1) | (z1 << 31))) + __popc(z1 & ((z1 >> 1) | (z2 << 31))) +
+                      __popc(z2 & ((z2 >> 1) | (z3 << 31))) + __popc(z3 & ((z3 >> 1) | (z4 << 31)));
+        if (i == 0 && d.J == 0) {
+            pc -= z0 & 1u;          // the number 1 is not a prime
+            tc -= z0 & (z0 >> 1) & 1u;  // nor is (1, 3) a twin pair
+        }
+        if (per_chunk) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                pc += __shfl_xor_sync(0xffffffffu, pc, o);
+                tc += __shfl_xor_sync(0xffffffffu, tc, o);
+            }
+            if (lane == 0) {
+                const uint64_t seg = (d.J + 128ull * (i - lane) - a.seg_j0) >> a.seg_l;
+                atomicAdd(&a.seg_primes[seg], (unsigned long long)pc);
+                if (a.seg_twins) atomicAdd(&a.seg_twins[seg], (unsigned long long)tc);
+            }
+        } else {
+            tp += pc;
+            tt += tc;
+        }
+    }
+    if (!per_chunk) {
+        // the tile lies in one segment: one pair of atomics per tile
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tp += __shfl_xor_sync(0xffffffffu, tp, o);
+            tt += __shfl_xor_sync(0xffffffffu, tt, o);
+        }
+        if (lane == 0) {
+            s_red[warp] = tp;
+            s_red[T / 32 + warp] = tt;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x = lane < T / 32 ? s_red[lane] : 0, y = lane < T / 32 ? s_red[T / 32 + lane] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+            }
+            if (lane == 0) {
+                const uint64_t seg = (d.J - a.seg_j0) >> a.seg_l;
+                atomicAdd(&a.seg_primes[seg], (unsigned long long)x);
+                if (a.seg_twins) atomicAdd(&a.seg_twins[seg], (unsigned long long)y);
+            }
+        }
+    }
+    if (tid == 0) {
+        const uint32_t first = (d.J == 0) ? 0u : (~sm[0] & 1u);
+        a.edge[t] = (uint8_t)(first | (((~sm[nwords - 1]) >> 31) << 1));
+    }
+    __syncthreads();
+}
+
 template <int T>
 __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_rho0[kMaxPresieveGroups];
-    __shared__ uint32_t s_red[T / 32];
+    __shared__ uint32_t s_red[2 * (T / 32)];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t ng = a.ps.ngroups;
 
@@ -322,6 +397,12 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
             }
         }
         __syncthreads();
+
+        // ---- count mode: primes and twin pairs per segment, no table written ----
+        if (!a.out) {
+            tile_counts<T>(sm, a, d, t, nwords, s_red);
+            continue;
+        }
 
         // ---- store (128-bit when aligned) and popcount ----
         uint32_t pop = 0;
@@ -964,6 +1045,27 @@ __global__ void k_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc
 cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st)
 {
     k_sum_u32<<<64, 256, 0, st>>>(v, n, acc);
+    return cudaGetLastError();
+}
+
+// twin pairs straddling tiles t and t+1 of one interval (count mode): the last bit of
+// tile t and the first bit of tile t+1 both primes; the pair belongs to the segment of
+// its lower member
+__global__ void k_seg_edges(const TileDesc *tiles, const uint8_t *edge, uint32_t ntiles, uint64_t seg_j0,
+                            uint32_t seg_l, unsigned long long *seg_twins)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t + 1 < ntiles; t += gridDim.x * blockDim.x) {
+        const TileDesc a = tiles[t];
+        if (a.J + a.len == tiles[t + 1].J && (edge[t] & 2) && (edge[t + 1] & 1))
+            atomicAdd(&seg_twins[(a.J + a.len - 1 - seg_j0) >> seg_l], 1ull);
+    }
+}
+
+cudaError_t launch_seg_edges(const TileDesc *tiles, const uint8_t *edge, uint32_t ntiles, uint64_t seg_j0,
+                             uint32_t seg_l, unsigned long long *seg_twins, cudaStream_t st)
+{
+    if (ntiles > 1) k_seg_edges<<<(ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024, 256, 0, st>>>(
+        tiles, edge, ntiles, seg_j0, seg_l, seg_twins);
     return cudaGetLastError();
 }
 

@@ -269,6 +269,16 @@ struct TileArgs {
     uint32_t run;
     uint32_t *carry_h;              // per CTA, per carried prime: wheel state << 29 | next hit offset
     uint32_t carry_stride;          // carried primes per CTA
+    // count mode (out == null): per segment of 2^seg_l bits from seg_j0 on, the primes
+    // (zero bits, the number 1 excluded) and twin pairs (adjacent zero bits, the lower
+    // one in the segment) of each finished tile are added to seg_primes / seg_twins;
+    // edge[t] gets bit 0 = "first bit is a prime", bit 1 = "last bit is a prime" for the
+    // pairs that straddle two tiles (k_seg_edges adds those)
+    unsigned long long *seg_primes;
+    unsigned long long *seg_twins;
+    uint8_t *edge;
+    uint64_t seg_j0;
+    uint32_t seg_l;
 };
 
 struct ScatterArgs {
@@ -315,5 +325,8 @@ cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned lon
 cudaError_t probe_smem_atomics(int nsm, double *atom_per_s);
 cudaError_t set_kernel_attributes();
 cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st);
+// twin pairs across the boundary of tiles t and t+1 of one interval (count mode)
+cudaError_t launch_seg_edges(const TileDesc *tiles, const uint8_t *edge, uint32_t ntiles, uint64_t seg_j0,
+                             uint32_t seg_l, unsigned long long *seg_twins, cudaStream_t st);
 
 }  // namespace gbs

@@ -94,6 +94,7 @@ def lib():
             "sieve_f_from_midpoint": (_i32, [_u32, _u64, _u64, _u32, ctypes.POINTER(_u64)]),
             "sieve_segments_midpoint": (_i32, [_vp, _u32, _u64, _u32, _u64, _vp, _vp]),
             "sieve_segments_host": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp]),
+            "sieve_count_segments": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp, _vp]),
             "sieve_count": (_i32, [_vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "sieve_sync": (_i32, [_vp, _vp]),
             "sieve_batch": (_i32, [_vp, ctypes.POINTER(Req), _u32, _vp, _vp, _vp]),
@@ -195,6 +196,14 @@ def sieve_segments(ctx, l, f, n, dev_bits, stream=None):
     _check(lib().sieve_segments(ctx.handle, l, f, n, _dev_ptr(dev_bits, "dev_bits", _table_bytes(l, n)),
                                 _stream(stream)),
            "sieve_segments")
+
+
+def sieve_count_segments(ctx, l, f, n, dev_primes, dev_twins=None, stream=None):
+    """Per-segment prime counts (and twin-pair counts when dev_twins is given) of the
+    interval (l, f, n), without writing its table: CUDA int64 tensors of n entries."""
+    _check(lib().sieve_count_segments(ctx.handle, l, f, n, _dev_ptr(dev_primes, "dev_primes", 8 * n),
+                                      _dev_ptr(dev_twins, "dev_twins", 8 * n) if dev_twins is not None else None,
+                                      _stream(stream)), "sieve_count_segments")
 
 
 def sieve_f_from_midpoint(l, n, mant, exp10):

@@ -3,13 +3,15 @@
 Calls only the CPU oracle (``oracle/``) and the seeded input generators; no value
 here comes from the CUDA path.  Run from the repository root:
 
-    python tests/golden/make_golden.py [c2] [c3] [c3full] [batch]
+    python tests/golden/make_golden.py [c2] [c2counts] [c3] [c3full] [batch]
 
 Outputs (text, one record per line):
   c2_segments.txt     l=20, n=8192, midpoint 1e15: per-segment composite counts,
                       plus the SHA-256 of the whole packed table.
   c3_samples.txt      l=20, n=32768, midpoint 2^60: 24 seeded segments, each with its
                       composite count and SHA-256.
+  c2_counts.txt       the l=20, n=8192, 1e15 table's per-segment prime and twin-pair
+                      counts (oracle.segment_counts).
   c3_segments.txt     the same table whole: per-segment composite counts and the
                       SHA-256 of all 2^35 bits (computed 512 segments at a time).
   batch_4096_seed0.txt  the 4096 seeded batch requests (j0, nbits) with each one's
@@ -50,6 +52,20 @@ def make_c2():
         fh.write("# total %d\n" % sum(counts))
         for t, c in enumerate(counts):
             fh.write("%d %d\n" % (t, c))
+
+
+def make_c2_counts():
+    l, n = 20, 8192
+    f = oracle.f_from_midpoint(l, n, 1, 15)
+    t0 = time.time()
+    w = oracle.sieve(l, f, n)
+    pr, tw = oracle.segment_counts(w, f << l, n << l, l)
+    with open(os.path.join(HERE, "c2_counts.txt"), "w") as fh:
+        fh.write("# l=20 n=8192 midpoint=1e15 f=%d: segment t, primes, twin pairs with the lower "
+                 "member in t (tests/golden/make_golden.py, CPU oracle, %.0f s)\n" % (f, time.time() - t0))
+        fh.write("# total %d %d\n" % (int(pr.sum()), int(tw.sum())))
+        for t in range(n):
+            fh.write("%d %d %d\n" % (t, pr[t], tw[t]))
 
 
 def make_c3(nsamples=24):
@@ -125,5 +141,5 @@ if __name__ == "__main__":
     which = sys.argv[1:] or ["c2", "c3", "batch"]
     for w in which:
         t = time.time()
-        {"c2": make_c2, "c3": make_c3, "c3full": make_c3_full, "batch": make_batch}[w]()
+        {"c2": make_c2, "c2counts": make_c2_counts, "c3": make_c3, "c3full": make_c3_full, "batch": make_batch}[w]()
         print(w, "done in %.0f s" % (time.time() - t), flush=True)
