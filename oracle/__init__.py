@@ -45,6 +45,8 @@ def _load():
         lib.oracle_is_composite_trial.argtypes = [_u64]
         lib.oracle_is_prime_mr.restype = ctypes.c_int
         lib.oracle_is_prime_mr.argtypes = [_u64]
+        lib.oracle_goldbach_min_p.restype = ctypes.c_int
+        lib.oracle_goldbach_min_p.argtypes = [_u64, _u64, ctypes.c_void_p, _u64, _u32, ctypes.c_void_p]
         lib.oracle_segment_counts.restype = ctypes.c_int
         lib.oracle_segment_counts.argtypes = [ctypes.c_void_p, _u64, _u64, _u32, ctypes.c_void_p,
                                               ctypes.c_void_p]
@@ -160,6 +162,33 @@ def segment_counts(words: np.ndarray, J0: int, nbits: int, l: int):
     if rc != 0:
         raise ValueError("oracle_segment_counts failed with code %d" % rc)
     return pr[:nseg].astype(np.int64), tw[:nseg].astype(np.int64)
+
+
+def goldbach_min_p(n_lo: int, count: int, p_max: int) -> np.ndarray:
+    """For each even N = n_lo + 2i (i < count) the smallest odd prime p <= p_max with
+    N - p prime (Miller-Rabin on N - p), 0 if none (oracle_goldbach_min_p)."""
+    primes = Base(max(3, p_max)).primes
+    out = np.zeros(max(int(count), 1), dtype=np.uint32)
+    rc = _load().oracle_goldbach_min_p(n_lo, count, primes.ctypes.data, len(primes), p_max, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_goldbach_min_p failed with code %d" % rc)
+    return out[:count]
+
+
+def goldbach_windows(n_lo: int, min_p: np.ndarray, win_log2: int):
+    """Per window of 2^win_log2 consecutive even numbers: (largest minimal p, the first N
+    attaining it, or None when no N of the window has a p; numbers with no p)."""
+    out = []
+    w = 1 << win_log2
+    for k in range(0, len(min_p), w):
+        part = np.asarray(min_p[k:k + w], dtype=np.int64)
+        fail = int((part == 0).sum())
+        mx = int(part.max())
+        if mx == 0:
+            out.append((0, None, fail))
+        else:
+            out.append((mx, int(n_lo) + 2 * (k + int(np.argmax(part == mx))), fail))
+    return out
 
 
 def get_bit(words: np.ndarray, j: int) -> int:

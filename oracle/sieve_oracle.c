@@ -310,3 +310,27 @@ int oracle_segment_counts(const uint32_t *words, uint64_t J0, uint64_t nbits, ui
     }
     return ORACLE_OK;
 }
+
+/* Goldbach search (Sec. 5: the sieve is made for verifying the Goldbach conjecture).
+ * For the even numbers N = n_lo + 2i, 0 <= i < count: min_p[i] = the smallest odd
+ * prime p among primes[0..nprimes) (ascending odd primes) with p <= p_max such that
+ * N - p is prime, decided by deterministic Miller-Rabin (oracle_is_prime_mr), not by a
+ * sieve; 0 when there is none.  Plain double loop. */
+int oracle_goldbach_min_p(uint64_t n_lo, uint64_t count, const uint32_t *primes, uint64_t nprimes,
+                          uint32_t p_max, uint32_t *min_p)
+{
+    if ((n_lo & 1) || (count && !min_p) || (nprimes && !primes)) return ORACLE_EINVAL;
+    for (uint64_t i = 0; i < count; ++i) {
+        const uint64_t N = n_lo + 2 * i;
+        min_p[i] = 0;
+        for (uint64_t k = 0; k < nprimes && primes[k] <= p_max; ++k) {
+            const uint64_t p = primes[k];
+            if (p + 3 > N) break; /* N - p >= 3: the smallest odd prime */
+            if (oracle_is_prime_mr(N - p)) {
+                min_p[i] = (uint32_t)p;
+                break;
+            }
+        }
+    }
+    return ORACLE_OK;
+}
