@@ -52,6 +52,7 @@ def parse():
                     help="arrival time per rate of the saturating serving sweep (0: no sweep)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2^60 sub-record of the default run")
     ap.add_argument("--fresh-steps", type=int, default=4, help="fresh-interval steps (0: none)")
+    ap.add_argument("--no-consumers", action="store_true", help="skip the count-only and Goldbach legs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1e12..1e18 midpoint sweep")
     ap.add_argument("--clocks-csv", default="",
                     help="where to keep the nvidia-smi samples of the timed region (default: a temp file)")
@@ -495,6 +496,74 @@ def measure_fresh(S, ctx, l, f, n, steps, host=False):
     return {"value": N * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps}
 
 
+def measure_consumers(S, ctx, l, f, n, steps):
+    """The consumers fused with the table (Sec. 5 uses of the sieve), each timed with CUDA
+    events after 3 warm-up calls:
+      count: per-segment prime and twin-pair counts of the workload interval without
+             writing its table (sieve_count_segments), odd numbers/s;
+      goldbach: the smallest-partition search for 2^30 consecutive even numbers around
+             10^18 on their table (sieve_segments of the odd numbers from N - p_max to
+             N - 3, then sieve_goldbach), even numbers/s for the search alone and with
+             the table's sieving."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pr = torch.empty(n, dtype=torch.int64, device="cuda")
+    tw = torch.empty(n, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        S.sieve_count_segments(ctx, l, f, n, pr, tw)
+    S.sieve_sync(ctx)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        S.sieve_count_segments(ctx, l, f, n, pr, tw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.sieve_sync(ctx)
+    t_count = ev0.elapsed_time(ev1) * 1e-3 / steps
+    count = {"value": (n << l) / t_count, "unit": "odd numbers/s", "ms_per_step": t_count * 1e3,
+             "primes": int(pr.sum().item()), "twin_pairs": int(tw.sum().item())}
+    del pr, tw
+
+    # Goldbach around 1e18: N = n_lo + 2i, i < 2^30; table from N_lo - p_max up
+    lg, cnt, p_max, win = 20, 1 << 30, 1 << 15, 20
+    n_lo = 10**18
+    lo_j = (n_lo - p_max - 1) // 2
+    hi_j = (n_lo + 2 * cnt) // 2
+    gf = lo_j >> lg
+    gn = (hi_j >> lg) + 1 - gf
+    tab = torch.empty((gn << lg) // 32, dtype=torch.int32, device="cuda")
+    nwin = ((cnt - 1) >> win) + 1
+    wins = torch.empty(2 * nwin, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        S.sieve_segments(ctx, lg, gf, gn, tab)
+        S.sieve_goldbach(ctx, tab, gf << lg, gn << lg, n_lo, cnt, p_max, win, wins)
+    S.sieve_sync(ctx)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        S.sieve_goldbach(ctx, tab, gf << lg, gn << lg, n_lo, cnt, p_max, win, wins)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_gb = ev0.elapsed_time(ev1) * 1e-3 / steps
+    ev0.record(stream)
+    for _ in range(steps):
+        S.sieve_segments(ctx, lg, gf, gn, tab)
+        S.sieve_goldbach(ctx, tab, gf << lg, gn << lg, n_lo, cnt, p_max, win, wins)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.sieve_sync(ctx)
+    t_both = ev0.elapsed_time(ev1) * 1e-3 / steps
+    dec = S.goldbach_windows(wins.cpu().tolist(), n_lo, win)
+    top = max(dec, key=lambda x: (x[0], -(x[1] or 0)))
+    gold = {"value": cnt / t_gb, "unit": "even numbers/s", "ms_per_step": t_gb * 1e3,
+            "with_sieve": cnt / t_both, "with_sieve_ms": t_both * 1e3, "n_lo": n_lo, "count": cnt,
+            "p_max": p_max, "max_min_p": top[0], "at": top[1], "failures": sum(x[2] for x in dec)}
+    del tab, wins
+    torch.cuda.empty_cache()
+    return {"count": count, "goldbach": gold}
+
+
 def measure_batch(S, ctx, args, rank, world, hbm_peak, r_atom):
     """args.batch_requests (4096) seeded requests of uneven length (2^16..2^28 numbers) and magnitude
     (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
@@ -665,9 +734,9 @@ def main():
     N = n << l
     vmax = 2 * ((f0 + world * n) << l)
     c3_on = args.workload == "c2" and not args.no_c3 and not args.segments
-    # the batch and serving legs draw requests up to ~1e18, the 2^60 sub-record sieves
-    # up to 2^60 + 2^35
-    wide = not (args.no_batch and args.no_serve and args.no_sweep) or c3_on
+    # the batch and serving legs draw requests up to ~1e18, the Goldbach leg works just
+    # above 1e18, the 2^60 sub-record sieves up to 2^60 + 2^35
+    wide = not (args.no_batch and args.no_serve and args.no_sweep and args.no_consumers) or c3_on
     ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 31)) if wide else vmax)
 
     tuned = None
@@ -744,6 +813,10 @@ def main():
               "steps": k3, "warmup": 3, **{k: m3[k] for k in ("roofline", "step_roofline", "kernels",
                                                              "clocks", "composites")}}
 
+    consumers = None
+    if rank == 0 and not args.no_consumers:
+        consumers = measure_consumers(S, ctx, l, f, n, max(2, min(args.steps, 5)))
+
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = measure_sweep(S, ctx, hbm_peak, r_atom)
@@ -770,7 +843,7 @@ def main():
             "gpu_launches": m["launches"],
             "roofline": m["roofline"], "step_roofline": m["step_roofline"], "kernels": m["kernels"],
             "cpu_baseline": base_line, "e2e": e2e, "fresh": fresh, "clocks": m["clocks"],
-            "c3": c3, "batch": batch, "serving": serving, "sweep": sweep,
+            "c3": c3, "consumers": consumers, "batch": batch, "serving": serving, "sweep": sweep,
             "composites": composites, "smem_atomic_peak_per_s": r_atom,
         }), flush=True)
     ctx.close()

@@ -112,6 +112,36 @@ sieve_status sieve_count_segments(sieve_ctx *ctx, uint32_t l, uint64_t f, uint64
                                   uint64_t *dev_primes, uint64_t *dev_twins, sieve_stream stream);
 
 /*
+ * Goldbach search on a finished table (Sec. 5: verifying the Goldbach conjecture is
+ * the use the authors built the sieve for).  dev_bits holds a table in the layout of
+ * sieve_segments: bit j (word j/32, bit j%32) stands for the odd number 2(j0 + j) + 1,
+ * 0 for primes (and the number 1), j < nbits (nbits % 32 == 0).  For every even
+ * N = n_lo + 2i, 0 <= i < count (n_lo even, >= 4), the device finds the smallest odd
+ * prime p <= p_max with N - p prime by reading the table, trying p = 3, 5, 7, ... in
+ * order.  Per window w of 2^win_log2 consecutive i (5 <= win_log2 <= 32) it writes
+ * dev_windows[w] (caller-owned device memory, ceil(count / 2^win_log2) entries, 8-byte
+ * aligned, overwritten):
+ *   key       (largest minimal p in the window) << 32 | (2^32 - 1 - k), k the offset
+ *             in the window of the first N attaining it; 0 when no N of the window
+ *             has such a p;
+ *   failures  even numbers of the window with no odd prime p <= p_max for which
+ *             N - p is prime (within p_max: a candidate counterexample, or p_max too
+ *             small).
+ * The table must hold N - 3 for the largest N, and, unless j0 == 0, N - p_max for the
+ * smallest N (SIEVE_ERANGE otherwise); p_max must not exceed the context's base limit
+ * (the primes tried are the context's resident base primes).  Asynchronous on
+ * `stream`; the table must be complete on that stream.  SIEVE_EINVAL for null or
+ * misaligned pointers, odd n_lo, count 0 or win_log2 out of range.
+ */
+typedef struct {
+    uint64_t key;
+    uint64_t failures;
+} sieve_goldbach_window;
+sieve_status sieve_goldbach(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t j0, uint64_t nbits,
+                            uint64_t n_lo, uint64_t count, uint32_t p_max, uint32_t win_log2,
+                            sieve_goldbach_window *dev_windows, sieve_stream stream);
+
+/*
  * End-to-end form of sieve_segments: the table lands in caller-owned HOST memory
  * host_bits (n*2^(l-5) words; pinned memory copies fastest).  The context sieves
  * it in epochs of at most 2^30 bits into a two-slot device ring and copies each

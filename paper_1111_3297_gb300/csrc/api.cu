@@ -263,7 +263,7 @@ void scratch_free(Scratch &s)
     if (s.s_tile) cudaStreamSynchronize(s.s_tile);
     if (s.s_scat) cudaStreamSynchronize(s.s_scat);
     for (int b = 0; b < 2; ++b)
-        for (void *p : {(void *)s.d_bkt[b], (void *)s.d_bkt_cnt[b], (void *)s.d_ovf[b]})
+        for (void *p : {s.ext_pools ? nullptr : (void *)s.d_bkt[b], (void *)s.d_bkt_cnt[b], (void *)s.d_ovf[b]})
             if (p) cudaFree(p);
     if (s.d_carry) cudaFree(s.d_carry);
     if (s.d_tcarry_h) cudaFree(s.d_tcarry_h);
@@ -289,7 +289,11 @@ sieve_status scratch_ensure(Scratch &s, uint64_t pool_entries, uint32_t max_epoc
         if (r) return r;
     }
     for (int b = 0; b < 2; ++b) {
-        sieve_status r = ensure((void **)&s.d_bkt[b], &s.bkt_bytes[b], (size_t)pool_entries * 4 + 64, &s.gen);
+        // external pools: the owner placed them (and sized them for pool_entries)
+        sieve_status r = s.ext_pools ? (s.d_bkt[b] && s.bkt_bytes[b] >= (size_t)pool_entries * 4 + 64 ? SIEVE_OK
+                                                                                                  : SIEVE_ENOMEM)
+                                     : ensure((void **)&s.d_bkt[b], &s.bkt_bytes[b], (size_t)pool_entries * 4 + 64,
+                                              &s.gen);
         if (r) return r;
         r = ensure((void **)&s.d_bkt_cnt[b], &s.bkt_cnt_bytes[b], (size_t)max_epoch_tiles * 4 + 64, &s.gen);
         if (r) return r;
@@ -525,6 +529,8 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     }
     close_group();
     close_epoch();
+    for (const SUDesc &u : P->sus)
+        if (u.span > kMaxUnitSpan || (uint64_t)u.tile_rel + ((u.span + B - 1) >> bt) > kScatterMaxTiles) return nullptr;
     for (const auto &e : P->epochs) P->max_epoch_tiles = std::max(P->max_epoch_tiles, e.ntiles);
     make_chunks(c, P.get());
     P->single_request = reqs.size() == 1;
@@ -1119,6 +1125,28 @@ try {
     return run_plan(c, P, nullptr, nullptr, (cudaStream_t)stream, true);
 } catch (...) {
     return SIEVE_ENOMEM;  // host memory (or another host resource) ran out
+}
+
+sieve_status sieve_goldbach(sieve_ctx *c, const uint32_t *dev_bits, uint64_t j0, uint64_t nbits, uint64_t n_lo,
+                            uint64_t count, uint32_t p_max, uint32_t win_log2, sieve_goldbach_window *dev_windows,
+                            sieve_stream stream)
+{
+    static_assert(sizeof(sieve_goldbach_window) == sizeof(GoldbachWindow), "window layout");
+    if (!c || !dev_bits || !dev_windows || ((uintptr_t)dev_windows & 7) || ((uintptr_t)dev_bits & 3) ||
+        count == 0 || (nbits & 31) || (n_lo & 1) || n_lo < 4 || p_max < 3 || win_log2 < 5 || win_log2 > 32)
+        return SIEVE_EINVAL;
+    if (p_max > c->base_limit || count > (~0ull - n_lo) / 2 || j0 + nbits < j0) return SIEVE_ERANGE;
+    const uint64_t n_hi = n_lo + 2 * (count - 1);
+    // the largest N - 3 and, unless the table starts at 1, the smallest N - p_max lie in it
+    if (n_hi / 2 - 2 >= j0 + nbits) return SIEVE_ERANGE;
+    if (j0 != 0 && (n_lo / 2 < (uint64_t)(p_max + 1) / 2 + j0)) return SIEVE_ERANGE;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t nwin = ((count - 1) >> win_log2) + 1;
+    CK(cudaMemsetAsync(dev_windows, 0, nwin * sizeof(sieve_goldbach_window), st));
+    CK(launch_goldbach(dev_bits, j0, nbits / 32, c->d_primes, prime_count_le(c, p_max), n_lo, count, win_log2,
+                       reinterpret_cast<GoldbachWindow *>(dev_windows), c->nsm, st));
+    return SIEVE_OK;
 }
 
 sieve_status sieve_f_from_midpoint(uint32_t l, uint64_t n, uint64_t mant, uint32_t exp10, uint64_t *f_out)

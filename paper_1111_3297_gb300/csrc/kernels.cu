@@ -1070,6 +1070,101 @@ cudaError_t launch_seg_edges(const TileDesc *tiles, const uint8_t *edge, uint32_
 }
 
 // ---------------------------------------------------------------------------
+// Goldbach search (Sec. 5: verifying the Goldbach conjecture is what the table is
+// made for).  For an even N and an odd prime p, N - p = 2J + 1 with J = N/2 - (p+1)/2,
+// so for 32 consecutive even numbers N_i = N_0 + 2i the candidates N_i - p are the 32
+// consecutive table bits from J_0 = N_0/2 - (p+1)/2 on: one 32-bit window of the table
+// (two words and a funnel shift) answers "is N_i - p prime" for all 32 at once (bit 0
+// = prime; the number 1, J = 0, is masked out).  Thread b takes N_i = n_lo + 2(32b + i)
+// and tries p = 3, 5, 7, ... in order, marking each number done at the first p whose
+// window bit is 0, so that p is its smallest partition prime.  It stops when all its
+// numbers are done, the primes run out, or the windows fall below the table (only
+// when the table starts at 1: then J < 0 means p > N - 1 and the number fails).  The
+// largest minimal p among its numbers is the p that completed the last of them, the
+// first N attaining it the lowest of the numbers completed by that p.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_goldbach(const uint32_t *__restrict__ bits, uint64_t j0, uint64_t nwords,
+                                                  const uint32_t *__restrict__ primes, uint32_t nprimes,
+                                                  uint64_t n_lo, uint64_t count, uint32_t win_log2,
+                                                  GoldbachWindow *out)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nblk = (count + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
+    // whole warps walk the blocks together (b - lane is the same for the 32 lanes), so
+    // the shuffles below are warp-uniform
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b - lane < nblk; b += stride) {
+        // valid: the block's numbers (fewer in the last block); alive: those that can
+        // still be done; done: those whose smallest partition prime has been found
+        uint32_t valid = 0, alive = 0, done = 0, p_last = 0, first_last = 0;
+        if (b < nblk) {
+            const uint64_t left = count - 32 * b;
+            valid = alive = left >= 32 ? 0xFFFFFFFFu : (1u << left) - 1u;
+            const int64_t hN = (int64_t)((n_lo >> 1) + 32 * b);  // N_0 / 2 (numbers below 2^63)
+            for (uint32_t k = 0; k < nprimes && (alive & ~done); ++k) {
+                const uint32_t p = __ldg(primes + k);
+                const int64_t Jw = hN - (int64_t)((p + 1) >> 1);  // J of N_0 - p
+                const int64_t jw = Jw - (int64_t)j0;               // relative to the table
+                uint32_t w;
+                if (jw >= 0) {
+                    const uint64_t q = (uint64_t)jw >> 5;
+                    const uint32_t lo = __ldg(bits + q);
+                    const uint32_t hi = q + 1 < nwords ? __ldg(bits + q + 1) : 0xFFFFFFFFu;
+                    w = __funnelshift_r(lo, hi, (uint32_t)jw & 31);
+                } else {
+                    // only when the table starts at 1 (j0 = 0): numbers i < -jw have
+                    // N_i - p < 1, and so for every larger p: they fail
+                    if (jw <= -32) break;
+                    const uint32_t sh = (uint32_t)(-jw), below = (1u << sh) - 1u;
+                    w = (__ldg(bits) << sh) | below;
+                    alive &= ~below | done;
+                }
+                uint32_t prime = ~w & alive & ~done;
+                if (Jw <= 0 && Jw > -32) prime &= ~(1u << (uint32_t)(-Jw));  // N_i - p = 1
+                if (prime) {
+                    done |= prime;
+                    p_last = p;
+                    first_last = __ffs(prime) - 1;
+                }
+            }
+        }
+        const uint32_t fail = __popc(valid & ~done);
+        const uint64_t off = (32 * b + first_last) & ((1ull << win_log2) - 1);
+        unsigned long long key = p_last ? ((unsigned long long)p_last << 32) | (0xFFFFFFFFull - off) : 0ull;
+        if (win_log2 >= 10) {
+            // a warp's 32 blocks (1024 numbers) lie in one window
+            uint32_t f = fail;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long kk = __shfl_xor_sync(0xffffffffu, key, o);
+                key = kk > key ? kk : key;
+                f += __shfl_xor_sync(0xffffffffu, f, o);
+            }
+            if (lane == 0) {
+                GoldbachWindow &wd = out[(32 * (b - lane)) >> win_log2];
+                if (key) atomicMax(&wd.key, key);
+                if (f) atomicAdd(&wd.failures, (unsigned long long)f);
+            }
+        } else if (b < nblk) {
+            // a block's 32 numbers lie in one window (win_log2 >= 5)
+            GoldbachWindow &wd = out[(32 * b) >> win_log2];
+            if (key) atomicMax(&wd.key, key);
+            if (fail) atomicAdd(&wd.failures, (unsigned long long)fail);
+        }
+    }
+}
+
+cudaError_t launch_goldbach(const uint32_t *bits, uint64_t j0, uint64_t nwords, const uint32_t *primes,
+                            uint32_t nprimes, uint64_t n_lo, uint64_t count, uint32_t win_log2, GoldbachWindow *out,
+                            int nsm, cudaStream_t st)
+{
+    const uint64_t want = ((count + 31) / 32 + 255) / 256;  // one thread per 32 even numbers
+    const uint32_t grid = (uint32_t)(want < (uint64_t)nsm * 8 ? want : (uint64_t)nsm * 8);
+    if (grid) k_goldbach<<<grid, 256, 0, st>>>(bits, j0, nwords, primes, nprimes, n_lo, count, win_log2, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // popcount of a table
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc)

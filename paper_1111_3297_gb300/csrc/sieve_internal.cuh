@@ -312,6 +312,10 @@ int tile_blocks_per_sm(uint32_t tile_log2);
 size_t tile_smem_bytes(uint32_t tile_log2);
 cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
 constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
+// a scatter unit spans at most 2^30 bits (SUDesc.span), so a unit's entry v = (tile
+// offset << tile_log2) + hit offset stays below 2^31 for every tile size
+constexpr uint64_t kMaxUnitSpan = 1ull << 30;
+static_assert(((uint64_t)kScatterMaxTiles << 20) <= kMaxUnitSpan, "a full scatter group of 2^20-bit tiles fits a unit");
 // run: the single-request kernel (every group one unit continuing the previous one)
 cudaError_t launch_scatter(const ScatterArgs &a, uint32_t nchunks, bool big_wheel, bool run, cudaStream_t st);
 cudaError_t launch_bootstrap(uint32_t *primes_out, uint32_t *count_out, cudaStream_t st);
@@ -325,6 +329,16 @@ cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned lon
 cudaError_t probe_smem_atomics(int nsm, double *atom_per_s);
 cudaError_t set_kernel_attributes();
 cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st);
+// Goldbach search on a finished table (kernels.cu, k_goldbach): per window of
+// 2^win_log2 even numbers, key = (largest minimal p) << 32 | (2^32 - 1 - offset of the
+// first even number attaining it), and the count of even numbers with no p <= p_max
+struct GoldbachWindow {
+    unsigned long long key;
+    unsigned long long failures;
+};
+cudaError_t launch_goldbach(const uint32_t *bits, uint64_t j0, uint64_t nwords, const uint32_t *primes,
+                            uint32_t nprimes, uint64_t n_lo, uint64_t count, uint32_t win_log2, GoldbachWindow *out,
+                            int nsm, cudaStream_t st);
 // twin pairs across the boundary of tiles t and t+1 of one interval (count mode)
 cudaError_t launch_seg_edges(const TileDesc *tiles, const uint8_t *edge, uint32_t ntiles, uint64_t seg_j0,
                              uint32_t seg_l, unsigned long long *seg_twins, cudaStream_t st);

@@ -95,6 +95,7 @@ def lib():
             "sieve_segments_midpoint": (_i32, [_vp, _u32, _u64, _u32, _u64, _vp, _vp]),
             "sieve_segments_host": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp]),
             "sieve_count_segments": (_i32, [_vp, _u32, _u64, _u64, _vp, _vp, _vp]),
+            "sieve_goldbach": (_i32, [_vp, _vp, _u64, _u64, _u64, _u64, _u32, _u32, _vp, _vp]),
             "sieve_count": (_i32, [_vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "sieve_sync": (_i32, [_vp, _vp]),
             "sieve_batch": (_i32, [_vp, ctypes.POINTER(Req), _u32, _vp, _vp, _vp]),
@@ -204,6 +205,32 @@ def sieve_count_segments(ctx, l, f, n, dev_primes, dev_twins=None, stream=None):
     _check(lib().sieve_count_segments(ctx.handle, l, f, n, _dev_ptr(dev_primes, "dev_primes", 8 * n),
                                       _dev_ptr(dev_twins, "dev_twins", 8 * n) if dev_twins is not None else None,
                                       _stream(stream)), "sieve_count_segments")
+
+
+def sieve_goldbach(ctx, dev_bits, j0, nbits, n_lo, count, p_max, win_log2, dev_windows, stream=None):
+    """Goldbach search on the table dev_bits (bits j0 .. j0+nbits-1) for the even numbers
+    n_lo + 2i, i < count: dev_windows is a CUDA int64 tensor of 2 * ceil(count / 2^win_log2)
+    entries (key, failures per window; decode with goldbach_windows)."""
+    nwin = ((int(count) - 1) >> int(win_log2)) + 1 if count > 0 else 0
+    _check(lib().sieve_goldbach(ctx.handle, _dev_ptr(dev_bits, "dev_bits", int(nbits) // 8), j0, nbits, n_lo,
+                                count, p_max, win_log2, _dev_ptr(dev_windows, "dev_windows", 16 * nwin),
+                                _stream(stream)), "sieve_goldbach")
+
+
+def goldbach_windows(windows, n_lo, win_log2):
+    """Decode sieve_goldbach's output (a host sequence of 2 * nwin int64): per window
+    (largest minimal p, the first even N attaining it, failures); (0, None, f) for a
+    window in which no N has a p."""
+    out = []
+    w = [int(x) & 0xFFFFFFFFFFFFFFFF for x in windows]
+    for k in range(len(w) // 2):
+        key, fail = w[2 * k], w[2 * k + 1]
+        if key == 0:
+            out.append((0, None, fail))
+            continue
+        off = 0xFFFFFFFF - (key & 0xFFFFFFFF)
+        out.append((key >> 32, int(n_lo) + 2 * ((k << int(win_log2)) + off), fail))
+    return out
 
 
 def sieve_f_from_midpoint(l, n, mant, exp10):
