@@ -106,6 +106,7 @@ struct Scratch {
     size_t tcarry_h_bytes = 0;
     uint64_t gen = 0;             // bumped when a buffer moves (captured graphs re-capture)
     uint64_t pool_entries = 0;    // capacity allowed per pool (entries)
+    bool ext_pools = false;       // d_bkt[] point into memory the owner manages (server arena)
     cudaStream_t s_tile = nullptr, s_scat = nullptr;  // high / low priority
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_scat[2] = {nullptr, nullptr},
                 ev_tile[2] = {nullptr, nullptr};

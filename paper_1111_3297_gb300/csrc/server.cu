@@ -3,8 +3,12 @@
 // One scheduler thread owns all device work of the server.  Requests wait in a
 // FIFO; whenever a lane (a stream with its own scratch) is free, the scheduler
 // admits requests from the head of the FIFO while their tables fit in the
-// server's table arena, plans them as one batch (the batched path of
-// sieve_batch) and launches it on that lane.  Lanes run concurrently, so a
+// server's device arena, plans them as one batch (the batched path of
+// sieve_batch), reserves the plan's two large-prime bucket pools in the same
+// arena and launches it on that lane.  Tables and buckets thus share one memory
+// cap: a batch is admitted only when both its tables and its buckets fit, its
+// buckets return to the arena when it completes, and its tables when the client
+// releases them.  Lanes run concurrently, so a
 // request that arrives while others are on the GPU starts as soon as a lane and
 // memory free up.  Completion is observed with cudaEventQuery (no blocking
 // waits), the composite counts come back in pinned memory, and the table stays
@@ -39,6 +43,11 @@ struct Arena {
         free_.clear();
         free_[0] = n;
         used = 0;
+    }
+    uint64_t largest() const {
+        uint64_t m = 0;
+        for (const auto &kv : free_) m = std::max(m, kv.second);
+        return m;
     }
     bool alloc(uint64_t n, uint64_t *off) {
         n = (n + kGranule - 1) / kGranule * kGranule;
@@ -93,7 +102,12 @@ struct Lane {
     std::unique_ptr<Plan> plan;
     std::vector<Req *> reqs;
     bool busy = false;
+    uint64_t bkt_off = 0, bkt_bytes = 0;  // the batch's bucket pools in the arena
 };
+
+// bytes of one bucket pool of `entries` slots in the arena (granule-aligned)
+uint64_t pool_bytes(uint64_t entries) { return (entries * 4 + 64 + kGranule - 1) / kGranule * kGranule; }
+constexpr uint64_t kMinPoolEntries = 4096;  // the planner's smallest pool
 
 }  // namespace
 
@@ -114,12 +128,33 @@ struct sieve_server {
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    uint64_t lane_max_entries = 0;  // largest bucket pool a lane's batch may take
+    // arena releases so far; a batch rolled back for want of bucket memory blocks
+    // admission until the next release (no replanning while nothing has changed)
+    uint64_t mem_epoch = 0, blocked_epoch = ~0ull;
     void loop();
-    bool launch(Lane &L, std::vector<Req *> &batch);
+    int launch(Lane &L, std::vector<Req *> &batch, bool others_busy);
     void complete(Lane &L);
+    bool head_fits();
 };
 
-bool sieve_server::launch(Lane &L, std::vector<Req *> &batch)
+// the head of the queue could be admitted now: its table and the smallest bucket
+// pools fit in the arena at once (called with mu held)
+bool sieve_server::head_fits()
+{
+    if (pending.empty()) return false;
+    uint64_t o1 = 0, o2 = 0;
+    if (!arena.alloc(pending.front()->bytes, &o1)) return false;
+    const bool ok = arena.alloc(2 * pool_bytes(kMinPoolEntries), &o2);
+    if (ok) arena.release(o2, 2 * pool_bytes(kMinPoolEntries));
+    arena.release(o1, pending.front()->bytes);
+    return ok;
+}
+
+// Returns 1 when the batch is on the GPU, 0 when it failed (its requests carry the
+// error; the caller completes the lane) and -1 when its bucket pools do not fit in
+// the arena now (the batch went back to the head of the queue, tables released).
+int sieve_server::launch(Lane &L, std::vector<Req *> &batch, bool others_busy)
 try {
     std::vector<ReqSpec> rs(batch.size());
     std::vector<uint64_t> vl(batch.size());
@@ -131,9 +166,51 @@ try {
     }
     std::stable_sort(rs.begin(), rs.end(), [&](const ReqSpec &a, const ReqSpec &b) { return vl[a.idx] > vl[b.idx]; });
     const sieve_tuning t = c->batch_tune.tile_log2 ? c->batch_tune : c->tune[tune_class(vmax)];
-    L.plan = build_plan(c, rs, t, L.scr.pool_entries);
+    L.plan = build_plan(c, rs, t, lane_max_entries);
+    sieve_status s = L.plan ? SIEVE_OK : SIEVE_ERANGE;
+    if (!s) {
+        // the plan's two bucket pools, from the arena the tables come from: as the plan
+        // wants them, else the largest free block when it still holds every tile's
+        // bucket (more epochs, same bits) or nothing else runs (tiles beyond the pool
+        // use the backstop list), else back to the queue until memory frees up
+        uint32_t max_cap = 0;
+        for (const TileDesc &d : L.plan->tiles) max_cap = std::max(max_cap, d.bkt_cap);
+        uint64_t entries = std::max<uint64_t>(L.plan->pool_entries, kMinPoolEntries), off = 0;
+        bool got;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            got = arena.alloc(2 * pool_bytes(entries), &off);
+            if (!got) {
+                const uint64_t half = arena.largest() / 2 / kGranule * kGranule;
+                const uint64_t fit = half >= 64 + 4 * kMinPoolEntries ? ((half - 64) / 4) & ~3ull : 0;
+                if (fit >= kMinPoolEntries && (fit >= max_cap || !others_busy)) {
+                    entries = fit;
+                    got = arena.alloc(2 * pool_bytes(entries), &off);
+                }
+            }
+            if (!got) {
+                // roll the batch back: tables released, requests to the head of the queue
+                for (size_t i = batch.size(); i-- > 0;) {
+                    Req *r = batch[i];
+                    arena.release(r->off, r->bytes);
+                    r->admitted = false;
+                    pending.push_front(r);
+                }
+                blocked_epoch = mem_epoch;
+                L.plan.reset();
+                return -1;
+            }
+        }
+        L.bkt_off = off;
+        L.bkt_bytes = 2 * pool_bytes(entries);
+        if (entries < L.plan->pool_entries) L.plan = build_plan(c, rs, t, entries);
+        L.scr.d_bkt[0] = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d_arena) + off);
+        L.scr.d_bkt[1] = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d_arena) + off + pool_bytes(entries));
+        L.scr.bkt_bytes[0] = L.scr.bkt_bytes[1] = pool_bytes(entries);
+        L.scr.pool_entries = entries;
+        if (!L.plan) s = SIEVE_ERANGE;
+    }
     Plan *P = L.plan.get();
-    sieve_status s = P ? SIEVE_OK : SIEVE_ERANGE;
     if (!s) s = scratch_ensure(L.scr, P->pool_entries, P->max_epoch_tiles, P->carry_entries);
     if (!s) s = upload_plan(c, P, L.st);
     if (!s) s = enqueue_plan(c, L.scr, P, d_arena, L.d_counts, (uint32_t)batch.size(), L.st);
@@ -149,9 +226,9 @@ try {
         cudaStreamSynchronize(L.st);
         for (Req *r : L.reqs) r->status = s;
         *L.h_err = 0;
-        return false;
+        return 0;
     }
-    return true;
+    return 1;
 } catch (...) {
     // host memory ran out while planning or enqueueing (this runs on the server's
     // thread, which an escaping exception would end): wait for whatever was
@@ -161,7 +238,7 @@ try {
     L.busy = true;
     for (Req *r : L.reqs) r->status = SIEVE_ENOMEM;
     *L.h_err = 0;
-    return false;
+    return 0;
 }
 
 void sieve_server::complete(Lane &L)
@@ -181,6 +258,10 @@ void sieve_server::complete(Lane &L)
     }
     L.reqs.clear();
     L.plan.reset();
+    if (L.bkt_bytes) arena.release(L.bkt_off, L.bkt_bytes), ++mem_epoch;  // the batch's buckets return
+    L.bkt_bytes = 0;
+    L.scr.d_bkt[0] = L.scr.d_bkt[1] = nullptr;
+    L.scr.bkt_bytes[0] = L.scr.bkt_bytes[1] = 0;
     L.busy = false;
     cv_done.notify_all();
 }
@@ -208,6 +289,7 @@ void sieve_server::loop()
             std::vector<Req *> batch;
             {
                 std::lock_guard<std::mutex> g(mu);
+                if (blocked_epoch == mem_epoch) break;  // nothing released since the last rollback
                 uint64_t bits = 0;
                 while (!pending.empty() && batch.size() < kMaxBatch && bits < kMaxBatchBits) {
                     Req *r = pending.front();
@@ -220,7 +302,11 @@ void sieve_server::loop()
                 }
             }
             if (batch.empty()) break;
-            if (!launch(L, batch)) complete(L);
+            bool others = false;
+            for (Lane &M : lanes) others |= (&M != &L) && M.busy;
+            const int r = launch(L, batch, others);
+            if (r < 0) break;  // buckets do not fit now: wait for a batch to finish
+            if (r == 0) complete(L);
             launched = true;
         }
         // 3. sleep until new work or a short poll interval
@@ -231,10 +317,9 @@ void sieve_server::loop()
             if (pending.empty()) break;
             if (!launched) {
                 // stopping, nothing in flight, and the head of the queue did not fit
-                uint64_t o = 0;
-                if (arena.alloc(pending.front()->bytes, &o)) {
-                    arena.release(o, pending.front()->bytes);
-                    continue;  // a table was released meanwhile: admit on the next pass
+                if (head_fits()) {
+                    blocked_epoch = ~0ull;  // memory was released meanwhile: admit on the next pass
+                    continue;
                 }
                 // only the client's release of held tables could make room, so the
                 // queued requests end now instead of holding destroy forever
@@ -254,7 +339,9 @@ void sieve_server::loop()
             if (any_busy)
                 cv_work.wait_for(g, std::chrono::microseconds(50));
             else
-                cv_work.wait_for(g, std::chrono::milliseconds(2), [&] { return stop || !pending.empty(); });
+                cv_work.wait_for(g, std::chrono::milliseconds(2), [&] {
+                    return stop || (!pending.empty() && blocked_epoch != mem_epoch);
+                });
         }
     }
 }
@@ -266,9 +353,13 @@ try {
     std::unique_ptr<sieve_server> S(new sieve_server());
     S->c = c;
     S->t0 = std::chrono::steady_clock::now();
-    // a quarter of the cap for the lanes' bucket pools, the rest for tables
+    // one arena of mem_cap bytes holds the admitted requests' tables and the running
+    // batches' bucket pools; a batch's two pools hold at most lane_pool bytes together
+    // (a quarter of the cap shared by the lanes, at most 4 GiB), and less when the plan
+    // needs less
     const uint64_t lane_pool = std::min<uint64_t>((uint64_t)4 << 30, mem_cap / 4 / max_inflight);
-    const uint64_t arena = mem_cap - lane_pool * max_inflight;
+    S->lane_max_entries = lane_pool / 8;
+    const uint64_t arena = mem_cap;
     if (cudaMalloc(&S->d_arena, arena) != cudaSuccess) {
         cudaGetLastError();
         return SIEVE_ENOMEM;
@@ -286,7 +377,8 @@ try {
             return SIEVE_ENOMEM;
         }
         *L.h_err = 0;
-        if (scratch_init(L.scr, lane_pool / 8, 1u << 20) != SIEVE_OK) {
+        L.scr.ext_pools = true;  // set before anything can free the scratch
+        if (scratch_init(L.scr, S->lane_max_entries, 1u << 20) != SIEVE_OK) {
             sieve_server_destroy(S.release());
             return SIEVE_ENOMEM;
         }
@@ -305,7 +397,8 @@ try {
     uint64_t vlast;
     sieve_status s = check_range(S->c, j0, nbits, &vlast);
     if (s) return s;
-    if ((nbits / 8 + kGranule) > S->arena.size) return SIEVE_ENOMEM;
+    // never admissible: its table and the smallest bucket pools exceed the whole arena
+    if (nbits / 8 + kGranule + 2 * pool_bytes(kMinPoolEntries) > S->arena.size) return SIEVE_ENOMEM;
     Req *r = new Req();
     r->j0 = j0;
     r->nbits = nbits;
@@ -360,7 +453,7 @@ try {
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->live.find(id);
     if (it == S->live.end() || !it->second->done) return SIEVE_EINVAL;
-    if (it->second->admitted) S->arena.release(it->second->off, it->second->bytes);
+    if (it->second->admitted) S->arena.release(it->second->off, it->second->bytes), ++S->mem_epoch;
     delete it->second;
     S->live.erase(it);
     S->cv_work.notify_one();

@@ -164,7 +164,7 @@ def test_server_destroy_returns_when_held_tables_block_the_queue(ctx):
     """A served result that is never released keeps its table in the arena.  A queued
     request that cannot fit beside it must not hold sieve_server_destroy forever: it
     ends with SIEVE_EBUSY and destroy returns."""
-    srv = S.Server(ctx, mem_cap=256 << 20, max_inflight=2)  # 192 MiB of table arena
+    srv = S.Server(ctx, mem_cap=256 << 20, max_inflight=2)  # 256 MiB for tables and buckets
     try:
         nb = 1 << 30  # 128 MiB of table each
         first = srv.submit(1 << 40, nb)
@@ -258,3 +258,35 @@ def test_server_lane_pool_smaller_than_one_tile_bucket(ctx):
             srv.close()
         for k in range(4):
             S.sieve_set_tuning(ctx, k, **saved[k])
+
+
+def test_server_admits_by_table_and_bucket_memory(ctx):
+    """Tables and bucket pools share the server's one arena.  A request whose table fits
+    but whose table and smallest bucket pools do not is refused at submission; requests
+    whose tables and buckets cannot all be resident at once wait, are admitted as
+    batches finish and tables are released, and each equals the plain call."""
+    cap = 512 << 20
+    srv = S.Server(ctx, mem_cap=cap, max_inflight=4)
+    try:
+        with pytest.raises(S.SieveError):
+            srv.submit(1 << 40, (cap - 20000) * 8 // 32 * 32)  # table < arena < table + buckets
+        nb = 3 << 28  # 96 MiB of table each: five fill the arena
+        f = S.sieve_f_from_midpoint(5, nb // 32 * 8, 1, 15)
+        reqs = [((f << 5) + k * nb, nb) for k in range(8)]
+        ids = {srv.submit(j0, n): (j0, n) for j0, n in reqs}
+        results, deadline = {}, time.time() + 180
+        while len(results) < len(ids) and time.time() < deadline:
+            for r in srv.poll(8, timeout_ms=200):
+                assert r["status"] == 0
+                results[r["id"]] = (r["composites"], sha(torch.as_tensor(
+                    _DevArray(r["dev_bits"], r["nbits"] // 32), device="cuda")))
+                srv.release(r["id"])
+        assert len(results) == len(ids)
+    finally:
+        srv.close()
+    for rid, (j0, n) in ids.items():
+        plain = torch.empty(n // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments(ctx, 5, j0 // 32, n // 32, plain)
+        S.sieve_sync(ctx)
+        assert results[rid] == (S.sieve_count(ctx, plain, n), sha(plain)), j0
+        del plain
