@@ -747,6 +747,11 @@ def main():
     elif not args.no_autotune:
         tuned = S.sieve_autotune(ctx, l, f, n)
     r_atom = S.sieve_probe_smem_atomics(local)
+    dsmem = {}
+    for c in (2, 4, 8):
+        own, ctas = S.sieve_probe_dsmem_atomics(local, c, peer=False)
+        peer, _ = S.sieve_probe_dsmem_atomics(local, c, peer=True)
+        dsmem["cluster%d" % c] = {"own_slice_per_s": own, "peer_slice_per_s": peer, "ctas": ctas}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -844,7 +849,7 @@ def main():
             "roofline": m["roofline"], "step_roofline": m["step_roofline"], "kernels": m["kernels"],
             "cpu_baseline": base_line, "e2e": e2e, "fresh": fresh, "clocks": m["clocks"],
             "c3": c3, "consumers": consumers, "batch": batch, "serving": serving, "sweep": sweep,
-            "composites": composites, "smem_atomic_peak_per_s": r_atom,
+            "composites": composites, "smem_atomic_peak_per_s": r_atom, "dsmem_probe": dsmem,
         }), flush=True)
     ctx.close()
     if pg:

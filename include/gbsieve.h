@@ -306,6 +306,18 @@ sieve_status sieve_profile_read(sieve_ctx *ctx, sieve_profile *out, sieve_stream
 sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s);
 
 /*
+ * Micro-benchmark of distributed shared memory (thread-block clusters; the cost that
+ * decides whether a segment larger than one SM's shared memory pays, Sec. 2.2: a larger
+ * segment leaves fewer primes large).  Clusters of cluster_size CTAs (2, 4 or 8) of
+ * 1024 threads and 128 KB each, as many as fit at once, OR single bits into
+ * conflict-free words through the cluster window: of their own CTA (peer = 0) or of
+ * the next rank in the cluster (peer = 1).  Returns ORs per second over the whole GPU
+ * and the CTAs that ran (*ctas).  Waits for the device.
+ */
+sieve_status sieve_probe_dsmem_atomics(int device, uint32_t cluster_size, int peer, double *atomics_per_s,
+                                       uint32_t *ctas);
+
+/*
  * Planner inspection on the host, without a device.  Builds the plan sieve_batch
  * builds for the requests `reqs` (rules as for sieve_batch): the work
  * decomposition of Sec. 1.3 (segments = tiles) and Sec. 2.2 (large primes in

@@ -1461,3 +1461,13 @@ sieve_status sieve_probe_smem_atomics(int device, double *atomics_per_s)
     CK(probe_smem_atomics(nsm, atomics_per_s));
     return SIEVE_OK;
 }
+
+sieve_status sieve_probe_dsmem_atomics(int device, uint32_t cluster_size, int peer, double *atomics_per_s,
+                                       uint32_t *ctas)
+{
+    if (!atomics_per_s || !ctas || cluster_size < 2 || cluster_size > 8 || (cluster_size & (cluster_size - 1)))
+        return SIEVE_EINVAL;
+    CK(cudaSetDevice(device));
+    CK(probe_dsmem_atomics(cluster_size, peer ? 1 : 0, atomics_per_s, ctas));
+    return SIEVE_OK;
+}

@@ -1253,6 +1253,98 @@ cudaError_t probe_smem_atomics(int nsm, double *atom_per_s)
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// distributed shared memory OR rate: clusters of C CTAs, every thread a stream of
+// conflict-free ORs into a cluster rank's shared memory through the cluster window
+// (mapa + red.shared::cluster), target = own rank (peer = 0) or the next rank (peer =
+// 1).  Cluster barriers at the start (every slice zeroed and every CTA running before
+// any remote access) and at the end (no remote access after a CTA may exit), reached
+// by every thread of every CTA.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(1024, 1) k_probe_dsmem(uint32_t *sink, int peer)
+{
+    extern __shared__ uint32_t pm[];
+    for (uint32_t i = threadIdx.x; i < kProbeWords; i += blockDim.x) pm[i] = 0;
+    cluster_barrier();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bit = 1u << ((threadIdx.x * 7u + blockIdx.x) & 31);
+    const uint32_t tgt = peer ? (cluster_rank() + 1) % cluster_size() : cluster_rank();
+    uint32_t base;
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(pm + (kProbeUnroll * 32) * (warp & 15) + lane);
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(base) : "r"(local), "r"(tgt));
+    for (int it = 0; it < kProbeTrips; ++it) {
+#pragma unroll
+        for (int k = 0; k < kProbeUnroll; ++k)
+            asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(base + 128u * k), "r"(bit)
+                         : "memory");
+    }
+    cluster_barrier();
+    uint32_t v = 0;
+    for (uint32_t i = threadIdx.x; i < kProbeWords; i += blockDim.x) v ^= pm[i];
+    if (v == 0x12345678u) sink[0] = v;
+}
+
+cudaError_t probe_dsmem_atomics(uint32_t csize, int peer, double *atom_per_s, uint32_t *ctas)
+{
+    uint32_t *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 16);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)kProbeWords * 4;
+    cudaFuncSetAttribute(k_probe_dsmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(1024);
+    cfg.gridDim = dim3(csize);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, k_probe_dsmem, &cfg);
+    if (e == cudaSuccess && ncl < 1) e = cudaErrorInvalidConfiguration;
+    float ms = 0;
+    if (e == cudaSuccess) {
+        cfg.gridDim = dim3(ncl * csize);
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        e = cudaLaunchKernelEx(&cfg, k_probe_dsmem, sink, peer);  // warm-up
+        cudaEventRecord(a);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = cudaLaunchKernelEx(&cfg, k_probe_dsmem, sink, peer);
+        cudaEventRecord(b);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    if (e == cudaSuccess) {
+        *atom_per_s = (double)ncl * csize * 1024.0 * kProbeTrips * kProbeUnroll * 5 / (ms * 1e-3);
+        *ctas = (uint32_t)(ncl * csize);
+    }
+    cudaFree(sink);
+    return e;
+}
+
 cudaError_t set_kernel_attributes()
 {
     const int big = (int)tile_smem_bytes(20);

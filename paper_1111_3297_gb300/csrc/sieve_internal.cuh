@@ -327,6 +327,7 @@ cudaError_t launch_barrett(const uint32_t *primes, uint64_t n, uint64_t *m, cuda
 cudaError_t launch_popcount(const uint32_t *words, uint64_t nwords, unsigned long long *acc,
                             uint32_t grid, cudaStream_t st);
 cudaError_t probe_smem_atomics(int nsm, double *atom_per_s);
+cudaError_t probe_dsmem_atomics(uint32_t csize, int peer, double *atom_per_s, uint32_t *ctas);
 cudaError_t set_kernel_attributes();
 cudaError_t launch_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *acc, cudaStream_t st);
 // Goldbach search on a finished table (kernels.cu, k_goldbach): per window of

@@ -108,6 +108,7 @@ def lib():
             "sieve_profile_enable": (_i32, [_vp, _i32]),
             "sieve_profile_read": (_i32, [_vp, ctypes.POINTER(Profile), _vp]),
             "sieve_probe_smem_atomics": (_i32, [_i32, ctypes.POINTER(_dbl)]),
+            "sieve_probe_dsmem_atomics": (_i32, [_i32, _u32, _i32, ctypes.POINTER(_dbl), ctypes.POINTER(_u32)]),
             "sieve_plan_describe": (_i32, [_vp, _u64, _u64, _u32, ctypes.POINTER(Req), _u32,
                                            ctypes.POINTER(Tuning), _u64, ctypes.POINTER(PlanInfo),
                                            ctypes.POINTER(PlanTile), _u64, ctypes.POINTER(PlanGroup), _u64,
@@ -336,6 +337,14 @@ def sieve_probe_smem_atomics(device=0):
     r = _dbl()
     _check(lib().sieve_probe_smem_atomics(device, ctypes.byref(r)), "sieve_probe_smem_atomics")
     return r.value
+
+
+def sieve_probe_dsmem_atomics(device=0, cluster_size=2, peer=True):
+    """(ORs per second, CTAs that ran) of the distributed shared memory probe."""
+    r, n = _dbl(), _u32()
+    _check(lib().sieve_probe_dsmem_atomics(device, cluster_size, 1 if peer else 0, ctypes.byref(r), ctypes.byref(n)),
+           "sieve_probe_dsmem_atomics")
+    return r.value, n.value
 
 
 def sieve_plan_describe(primes, max_v, nsm, reqs, tuning=None, pool_entries=1 << 31, records=True):
