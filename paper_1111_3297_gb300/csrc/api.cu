@@ -651,6 +651,9 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         if (P->seg_twins) CK(cudaMemsetAsync(P->seg_twins, 0, (size_t)P->nsegs * 8, st));
     }
     bool run_first = true;
+    size_t last_scatter = 0;  // the last epoch with a scatter launch
+    for (size_t ei = 0; ei < P->epochs.size(); ++ei)
+        if (P->epochs[ei].ng) last_scatter = ei;
     for (size_t ei = 0; ei < P->epochs.size(); ++ei) {
         const Plan::Epoch &e = P->epochs[ei];
         const int b = (int)(ei & 1);
@@ -671,6 +674,7 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.state = scr.d_carry;
             sa.state_base = P->state_base;
             sa.run_first = run_first ? 1u : 0u;
+            sa.run_last = ei == last_scatter ? 1u : 0u;
             run_first = false;
             sa.wheel.gapw = c->d_gapw;
             sa.wheel.rstate = c->d_rstate;

@@ -802,6 +802,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         const GroupDesc g = a.groups[gi];
         const SUDesc u = a.sus[g.su0];
         const bool first = a.run_first && gi == 0;
+        const bool last = a.run_last && gi + 1 == a.ngroups;  // nothing reads the state after it
         const uint32_t span = u.span, ebase = u.tile_rel << bt;
         const uint32_t jsx = u.jw;
         scatter_group_setup(a, g, sh);
@@ -868,7 +869,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                 // next hit relative to the next group (h < span + 11 p < 2^48 unless none)
                 // with the wheel position (a lane that emitted nothing kept its own)
                 if (BIG && gw) s = big_wheel_pos(gw, gwi);
-                if (idx < n) stw[idx] = ((unsigned long long)s << 48) | (h == kRunInf ? kRunInf : h - span);
+                if (idx < n && !last) stw[idx] = ((unsigned long long)s << 48) | (h == kRunInf ? kRunInf : h - span);
                 lg += kScNW;
                 need = true;
             }

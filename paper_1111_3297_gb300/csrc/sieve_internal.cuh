@@ -296,6 +296,7 @@ struct ScatterArgs {
     unsigned long long *state;
     uint32_t state_base;
     uint32_t run_first;
+    uint32_t run_last;              // 1 when the launch's last group is the interval's last (no state after it)
     BigWheel wheel;
     uint32_t *bkt;
     uint32_t *bkt_cnt;
