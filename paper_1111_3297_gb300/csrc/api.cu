@@ -193,7 +193,7 @@ sieve_tuning default_tuning(uint32_t cls)
 
 bool tuning_valid(const sieve_tuning &t)
 {
-    return t.tile_log2 >= 12 && t.tile_log2 <= 20 && t.presieve_groups >= 1 &&
+    return t.tile_log2 >= 12 && t.tile_log2 <= kMaxTileLog2 && t.presieve_groups >= 1 &&
            t.presieve_groups <= (uint32_t)kMaxPresieveGroups && t.medium_max <= (1u << 28) &&
            t.window_tiles >= 1 && t.window_tiles <= kScatterMaxTiles &&
            ((uint64_t)t.window_tiles << t.tile_log2) <= (1ull << 30) && t.epoch_tiles >= t.window_tiles &&
@@ -365,6 +365,9 @@ static void make_chunks(sieve_ctx *c, Plan *P)
 
 std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs, sieve_tuning t, uint64_t pool_cap_in)
 {
+    // cluster tiles (beyond 2^20 bits) only for one interval, whose tiles a cluster walks
+    // in order; several requests take 2^20-bit tiles
+    if (reqs.size() != 1 && t.tile_log2 > 20) t.tile_log2 = 20;
     const uint32_t bt = t.tile_log2;
     const uint64_t B = 1ull << bt;
     {
@@ -389,8 +392,10 @@ std::unique_ptr<Plan> build_plan(sieve_ctx *c, const std::vector<ReqSpec> &reqs,
     {
         // primes whose 60-multiple warp step fits four times into the tile slice of
         // one warp are struck by the whole CTA
+        // (per CTA: a cluster tile's CTAs strike these primes on their own 2^20-bit slices)
         const uint32_t nw = (uint32_t)tile_threads(t.tile_log2) / 32;
-        P->blk_hi = std::max(P->med_lo, std::min(P->coop_hi, prime_count_le(c, (1ull << t.tile_log2) / (240 * nw))));
+        const uint64_t cta_bits = 1ull << std::min<uint32_t>(t.tile_log2, 20);
+        P->blk_hi = std::max(P->med_lo, std::min(P->coop_hi, prime_count_le(c, cta_bits / (240 * nw))));
     }
     const uint32_t large_lo = std::max(P->med_lo, prime_count_le(c, t.medium_max));
     const uint64_t pool_cap = pool_cap_in ? pool_cap_in : c->scr.pool_entries;
@@ -728,10 +733,25 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             const uint32_t run = (e.ntiles + tgrid - 1) / tgrid;
             if (((uint64_t)run << bt) < (1ull << 29) - 1) ta.run = run;
         }
+        uint32_t nclusters = 0;
+        if (bt > 20) {
+            // cluster tiles: every cluster a contiguous run of tiles (both CTAs walk the
+            // same ones), next hits carried inside the run
+            const uint32_t maxc = (uint32_t)ctile_max_clusters();
+            if (!maxc || !P->single_request || P->count_mode || (P->lane_stride && !scr.d_tcarry_h))
+                return SIEVE_EINVAL;
+            const uint32_t run = (e.ntiles + std::min(maxc, e.ntiles) - 1) / std::min(maxc, e.ntiles);
+            if (((uint64_t)run << bt) >= (1ull << 29) - 1) return SIEVE_ERANGE;
+            ta.run = run;
+            nclusters = (e.ntiles + run - 1) / run;
+        }
         // host output: the slot's previous copy must be done before the tiles overwrite it
         if (P->host_out && ei >= 2) CK(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
         prof_mark(c, prof, SIEVE_K_TILE, st, true);
-        CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));
+        if (bt > 20)
+            CK(launch_ctiles(ta, nclusters, st));
+        else
+            CK(launch_tiles(ta, ta.run ? (e.ntiles + ta.run - 1) / ta.run : tgrid, st));
         prof_mark(c, prof, SIEVE_K_TILE, st, false);
         CK(cudaEventRecord(scr.ev_tile[b], st));
         if (P->host_out) {
@@ -1109,7 +1129,12 @@ try {
     CK(cudaSetDevice(c->device));
     // tiles of >= 2^12 bits (tuning ranges) start 2^12-aligned relative to j0 and, since
     // 2^l >= 2^12 divides nbits, every tile is whole 4096-bit chunks of one segment
-    const sieve_tuning t = tuning_for(c, vlast, nbits);
+    sieve_tuning t = tuning_for(c, vlast, nbits);
+    if (t.tile_log2 > 20) {
+        // the count mode runs in the one-CTA tile kernel
+        t.tile_log2 = 20;
+        while (((uint64_t)t.window_tiles << t.tile_log2) > (1ull << 30)) t.window_tiles >>= 1;
+    }
     char key[200];
     std::snprintf(key, sizeof key, "C/%llu/%llu/%u/%p/%p/", (unsigned long long)j0, (unsigned long long)nbits, l,
                   (void *)dev_primes, (void *)dev_twins);

@@ -192,6 +192,130 @@ __device__ __forceinline__ void tile_counts(const uint32_t *sm, const TileArgs &
     __syncthreads();
 }
 
+// thread-block cluster helpers (PTX: %cluster_ctarank, %cluster_nctarank, barrier.cluster)
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Pre-sieve of the words [0, nwords) of a tile (or cluster slice) starting at index J.
+template <int T>
+__device__ __forceinline__ void presieve_tile(uint32_t *sm, const TileArgs &a, uint32_t *s_rho0, uint64_t J,
+                                              uint32_t nwords)
+{
+    const uint32_t tid = threadIdx.x;
+    const uint32_t ng = a.ps.ngroups;
+    // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
+    // Passes of at most 7 groups (fewer live residues per thread), each compiled
+    // for its exact groups; the second pass ORs into the words the first wrote.
+    if (tid < ng) s_rho0[tid] = mod_barrett(J, a.ps.modulus[tid], a.ps.barrett[tid]);
+    __syncthreads();
+    switch (ng < 7 ? ng : 7) {
+    case 1: presieve_pass<T, 0, 1>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    case 2: presieve_pass<T, 0, 2>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    case 3: presieve_pass<T, 0, 3>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    case 4: presieve_pass<T, 0, 4>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    case 5: presieve_pass<T, 0, 5>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    case 6: presieve_pass<T, 0, 6>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    default: presieve_pass<T, 0, 7>(sm, a, s_rho0, nwords, ng <= 7, J); break;
+    }
+    switch (ng > 7 ? ng - 7 : 0) {
+    case 0: break;
+    case 1: presieve_pass<T, 7, 1>(sm, a, s_rho0, nwords, true, J); break;
+    case 2: presieve_pass<T, 7, 2>(sm, a, s_rho0, nwords, true, J); break;
+    case 3: presieve_pass<T, 7, 3>(sm, a, s_rho0, nwords, true, J); break;
+    case 4: presieve_pass<T, 7, 4>(sm, a, s_rho0, nwords, true, J); break;
+    case 5: presieve_pass<T, 7, 5>(sm, a, s_rho0, nwords, true, J); break;
+    default: presieve_pass<T, 7, 6>(sm, a, s_rho0, nwords, true, J); break;
+    }
+    __syncthreads();
+}
+
+// Medium primes with many hits per tile, struck by the whole CTA and by one warp per
+// prime, over the len bits of a tile (or cluster slice) starting at index J.
+template <int T>
+__device__ __forceinline__ void strike_small_medium(uint32_t *sm, const TileArgs &a, uint64_t J, uint32_t len,
+                                                    uint32_t med_hi)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // ---- medium primes (Sec. 2.1, Sec. 3.2), wheel of Sec. 3.2.1 ----
+    // A lane strikes the (lane%8)-th admissible multiple of wheel period lane/8
+    // (a period is 15 multiples of p, 8 of them admissible), so a warp covers 4
+    // periods = 60 multiples of p per step.
+    const uint32_t js15 = (uint32_t)(J % 15u);
+    const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
+    {
+        // smallest primes: every warp takes every prime and strikes every NW-th
+        // step of it (warp w: steps w, w + NW, ...), so the work of one prime is
+        // spread over the whole CTA and a warp's start is one multiply-add
+        constexpr uint32_t NW = T / 32;
+        const uint32_t blk_end = min(a.blk_hi, med_hi);
+        for (uint32_t b = a.med_lo; b < blk_end; b += 32) {
+            const uint32_t idx = b + lane;
+            uint32_t p = 0, h = len, s = 0;
+            if (idx < blk_end) {
+                p = a.primes[idx];
+                const uint64_t hh = first_hit(J, js15, p, a.barrett[idx], s);
+                h = hh < len ? (uint32_t)hh : len;
+            }
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
+                const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
+                const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
+                if (hj >= len) continue;
+                // the host gives this phase primes with 4 * NW steps <= the tile, so
+                // pos stays below len + NW * step < 2^21
+                const uint32_t step = 60u * pj, stride = NW * step;
+                uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj + warp * step;
+                while (pos < len) {
+                    atomicOr(&sm[pos >> 5], 1u << (pos & 31));
+                    pos += stride;
+                }
+            }
+        }
+    }
+    {
+        // one prime per warp at a time; a warp's 32 primes are dealt round-robin
+        // from the whole range so that the warps' loads even out
+        constexpr uint32_t NW = T / 32;
+        const uint32_t lo = max(a.med_lo, a.blk_hi);
+        const uint32_t coop_end = min(a.coop_hi, med_hi);
+        for (uint32_t b = lo; b < coop_end; b += 32 * NW) {
+            const uint32_t idx = b + lane * NW + warp;
+            uint32_t p = 0, h = len, s = 0;
+            if (idx < coop_end) {
+                p = a.primes[idx];
+                const uint64_t hh = first_hit(J, js15, p, a.barrett[idx], s);
+                h = hh < len ? (uint32_t)hh : len;
+            }
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
+                const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
+                const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
+                if (hj >= len) continue;
+                uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
+                const uint32_t step = 60u * pj;
+                while (pos < len) {
+                    atomicOr(&sm[pos >> 5], 1u << (pos & 31));
+                    pos += step;
+                }
+            }
+        }
+    }
+}
+
 template <int T>
 __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
 {
@@ -218,95 +342,10 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
         const uint32_t len = d.len, nwords = len >> 5;
         const bool carried = a.run && it > 0;  // the previous tile of this CTA ends where d starts
 
-        // ---- pre-sieve: OR of the small-prime patterns (Sec. 3.1) ----
-        // Passes of at most 7 groups (fewer live residues per thread), each compiled
-        // for its exact groups; the second pass ORs into the words the first wrote.
-        if (tid < ng) s_rho0[tid] = mod_barrett(d.J, a.ps.modulus[tid], a.ps.barrett[tid]);
-        __syncthreads();
-        switch (ng < 7 ? ng : 7) {
-        case 1: presieve_pass<T, 0, 1>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        case 2: presieve_pass<T, 0, 2>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        case 3: presieve_pass<T, 0, 3>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        case 4: presieve_pass<T, 0, 4>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        case 5: presieve_pass<T, 0, 5>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        case 6: presieve_pass<T, 0, 6>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        default: presieve_pass<T, 0, 7>(sm, a, s_rho0, nwords, ng <= 7, d.J); break;
-        }
-        switch (ng > 7 ? ng - 7 : 0) {
-        case 0: break;
-        case 1: presieve_pass<T, 7, 1>(sm, a, s_rho0, nwords, true, d.J); break;
-        case 2: presieve_pass<T, 7, 2>(sm, a, s_rho0, nwords, true, d.J); break;
-        case 3: presieve_pass<T, 7, 3>(sm, a, s_rho0, nwords, true, d.J); break;
-        case 4: presieve_pass<T, 7, 4>(sm, a, s_rho0, nwords, true, d.J); break;
-        case 5: presieve_pass<T, 7, 5>(sm, a, s_rho0, nwords, true, d.J); break;
-        default: presieve_pass<T, 7, 6>(sm, a, s_rho0, nwords, true, d.J); break;
-        }
-        __syncthreads();
+        presieve_tile<T>(sm, a, s_rho0, d.J, nwords);
 
-        // ---- medium primes (Sec. 2.1, Sec. 3.2), wheel of Sec. 3.2.1 ----
-        // A lane strikes the (lane%8)-th admissible multiple of wheel period lane/8
-        // (a period is 15 multiples of p, 8 of them admissible), so a warp covers 4
-        // periods = 60 multiples of p per step.
         const uint32_t js15 = (uint32_t)(d.J % 15u);
-        const uint32_t cum_shift = 4u * (lane & 7), lane_base = 15u * (lane >> 3);
-        {
-            // smallest primes: every warp takes every prime and strikes every NW-th
-            // step of it (warp w: steps w, w + NW, ...), so the work of one prime is
-            // spread over the whole CTA and a warp's start is one multiply-add
-            constexpr uint32_t NW = T / 32;
-            const uint32_t blk_end = min(a.blk_hi, d.med_hi);
-            for (uint32_t b = a.med_lo; b < blk_end; b += 32) {
-                const uint32_t idx = b + lane;
-                uint32_t p = 0, h = len, s = 0;
-                if (idx < blk_end) {
-                    p = a.primes[idx];
-                    const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
-                    h = hh < len ? (uint32_t)hh : len;
-                }
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
-                    const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
-                    const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
-                    if (hj >= len) continue;
-                    // the host gives this phase primes with 4 * NW steps <= the tile, so
-                    // pos stays below len + NW * step < 2^21
-                    const uint32_t step = 60u * pj, stride = NW * step;
-                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj + warp * step;
-                    while (pos < len) {
-                        atomicOr(&sm[pos >> 5], 1u << (pos & 31));
-                        pos += stride;
-                    }
-                }
-            }
-        }
-        {
-            // one prime per warp at a time; a warp's 32 primes are dealt round-robin
-            // from the whole range so that the warps' loads even out
-            constexpr uint32_t NW = T / 32;
-            const uint32_t lo = max(a.med_lo, a.blk_hi);
-            const uint32_t coop_end = min(a.coop_hi, d.med_hi);
-            for (uint32_t b = lo; b < coop_end; b += 32 * NW) {
-                const uint32_t idx = b + lane * NW + warp;
-                uint32_t p = 0, h = len, s = 0;
-                if (idx < coop_end) {
-                    p = a.primes[idx];
-                    const uint64_t hh = first_hit(d.J, js15, p, a.barrett[idx], s);
-                    h = hh < len ? (uint32_t)hh : len;
-                }
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t hj = __shfl_sync(0xffffffffu, h, j);
-                    const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
-                    const uint32_t sj = __shfl_sync(0xffffffffu, s, j);
-                    if (hj >= len) continue;
-                    uint32_t pos = hj + (lane_base + ((c_cum[sj] >> cum_shift) & 15u)) * pj;
-                    const uint32_t step = 60u * pj;
-                    while (pos < len) {
-                        atomicOr(&sm[pos >> 5], 1u << (pos & 31));
-                        pos += step;
-                    }
-                }
-            }
-        }
+        strike_small_medium<T>(sm, a, d.J, len, d.med_hi);
         {
             // one prime per thread, the next prime's loads issued ahead; in a run of
             // tiles the next hit carries over (relative to the next tile's start)
@@ -438,8 +477,211 @@ __global__ void __launch_bounds__(T, 2048 / T) k_tile(TileArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster tile kernel: one segment of up to C * 2^20 bits held across the shared
+// memory of a cluster of C CTAs (Sec. 2.2: a larger segment leaves fewer primes
+// large), CTA rank r owning the slice [r * 2^20, (r+1) * 2^20).  Each CTA pre-sieves
+// its own slice and strikes the primes with many hits per slice there (the CTA-wide
+// and warp-per-prime phases, on its slice alone).  The one-prime-per-thread primes
+// and the drained bucket entries cover the whole segment: the C CTAs split them,
+// and a strike in another rank's slice is an OR through the cluster window
+// (red.shared::cluster).  Every index into a slice is masked to the slice and every
+// rank to the cluster, so no access leaves the cluster's shared memory whatever the
+// entries hold.
+// Cluster barriers: A after the pre-sieve (a slice is written before any rank ORs
+// into it), B after the last strike (before the slices are stored).  The next
+// tile's remote ORs come after its barrier A, which each CTA reaches only after
+// storing its slice.  Cluster c takes the tiles [c * run, (c+1) * run) in order
+// (one interval, each tile starting where the previous one ends), so both CTAs of a
+// cluster walk the same tiles and reach both barriers the same number of times, on
+// every path; a cluster without tiles reaches none.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(1024, 1) k_ctile(TileArgs a)
+{
+    static_assert(C == 2, "two-CTA clusters");
+    constexpr int T = 1024;
+    constexpr uint32_t SL = 1u << 20;  // bits per slice
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t s_rho0[kMaxPresieveGroups];
+    __shared__ uint32_t s_red[T / 32];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t rank = cluster_rank() & (C - 1);
+    uint32_t cid;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    // cluster-window addresses of the two slices
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(sm);
+    uint32_t win0, win1;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(win0) : "r"(local));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 1;" : "=r"(win1) : "r"(local));
+
+    // one bit into slice word (pos & (SL-1)) >> 5 of rank (pos >> 20) & (C-1)
+    auto strike = [&](uint32_t pos) {
+        const uint32_t owner = (pos >> 20) & (C - 1), loc = pos & (SL - 1);
+        const uint32_t bit = 1u << (loc & 31);
+        if (owner == rank) {
+            atomicOr(&sm[loc >> 5], bit);
+        } else {
+            const uint32_t addr = (owner ? win1 : win0) + ((loc >> 5) << 2);
+            asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(bit) : "memory");
+        }
+    };
+
+    const uint32_t run_lo = cid * a.run;
+    const uint32_t run_hi = min(a.ntiles, run_lo + a.run);
+    for (uint32_t it = 0; run_lo + it < run_hi; ++it) {
+        const uint32_t t = run_lo + it;
+        const TileDesc d = a.tiles[t];
+        const uint32_t len = d.len;
+        const uint64_t Js = d.J + (uint64_t)rank * SL;
+        const uint32_t lens = len > rank * SL ? min(SL, len - rank * SL) : 0u;
+        const bool carried = it > 0;  // the cluster's previous tile ends where d starts
+
+        presieve_tile<T>(sm, a, s_rho0, Js, lens >> 5);
+        cluster_barrier();  // A
+        strike_small_medium<T>(sm, a, Js, lens, d.med_hi);
+
+        {
+            // one prime per thread over the whole segment, the two CTAs taking alternate
+            // blocks of T primes; next hits carried from tile to tile as in k_tile
+            const uint32_t js15 = (uint32_t)(d.J % 15u);
+            const uint32_t end = d.med_hi;
+            const uint32_t lo = max(max(a.med_lo, a.blk_hi), a.coop_hi);
+            uint32_t *ch = a.carry_h + (size_t)blockIdx.x * a.carry_stride - lo;
+            for (uint32_t idx = lo + rank * T + tid; idx < end; idx += C * T) {
+                const uint32_t p = a.primes[idx];
+                constexpr uint32_t kNone = 0xFFFFFFFFu;
+                uint32_t s = 0, h;
+                if (carried) {
+                    const uint32_t cc = ch[idx];
+                    s = cc >> 29;
+                    h = (cc & 0x1FFFFFFFu) == 0x1FFFFFFFu ? kNone : (cc & 0x1FFFFFFFu);
+                } else {
+                    const uint64_t f = first_hit(d.J, js15, p, a.barrett[idx], s);
+                    h = f < (uint64_t)len + 0x1FFFFFFFu ? (uint32_t)f : kNone;
+                }
+                if (h < len) {
+                    uint32_t gq = __funnelshift_r(kGapPacked * 0x10001u, kGapPacked * 0x10001u, 2 * s), k = 0;
+                    for (;;) {
+                        strike(h);
+                        h += (gq & 3u) * p;
+                        gq = __funnelshift_r(gq, gq, 2);
+                        ++k;
+                        if (h >= len) break;
+                    }
+                    s = (s + k) & 7;
+                }
+                const uint32_t off = h >= len + 0x1FFFFFFFu ? 0x1FFFFFFFu : h - len;
+                ch[idx] = (s << 29) | off;
+            }
+        }
+
+        // ---- the segment's large-prime bucket, entries split between the CTAs ----
+        if (d.bkt_cap) {
+            const uint32_t cnt = min(a.bkt_cnt[t], d.bkt_cap);
+            const uint32_t *e = a.bkt + d.bkt_off;
+            const uint32_t n4 = cnt >> 2;
+            const uint4 *e4 = reinterpret_cast<const uint4 *>(e);
+#pragma unroll 4
+            for (uint32_t i = rank * T + tid; i < n4; i += C * T) {
+                const uint4 v = __ldcs(e4 + i);
+                strike(v.x);
+                strike(v.y);
+                strike(v.z);
+                strike(v.w);
+            }
+            for (uint32_t i = 4 * n4 + rank * T + tid; i < cnt; i += C * T) strike(__ldcs(e + i));
+            const uint32_t oc = min(*(volatile const uint32_t *)a.ovf_cnt, a.ovf_cap);
+            for (uint32_t i = rank * T + tid; i < oc; i += C * T) {
+                const unsigned long long x = a.ovf[i];
+                if ((uint32_t)(x >> 32) == t) strike((uint32_t)x);
+            }
+        }
+        __syncthreads();    // every warp converged before the cluster barrier
+        cluster_barrier();  // B
+
+        // ---- store the own slice (128-bit when aligned) and popcount ----
+        const uint32_t nwords = lens >> 5;
+        uint32_t pop = 0;
+        uint32_t *out = a.out + d.out_word + (size_t)rank * (SL / 32);
+        if (((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((nwords & 3) == 0)) {
+            uint4 *o4 = reinterpret_cast<uint4 *>(out);
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(sm);
+            for (uint32_t i = tid; i < (nwords >> 2); i += T) {
+                const uint4 v = s4[i];
+                o4[i] = v;
+                pop += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        } else {
+            for (uint32_t i = tid; i < nwords; i += T) {
+                const uint32_t v = sm[i];
+                out[i] = v;
+                pop += __popc(v);
+            }
+        }
+        if (a.req_counts) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
+            if (lane == 0) s_red[warp] = pop;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t v = s_red[lane];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && v) atomicAdd(&a.req_counts[d.req], (unsigned long long)v);
+            }
+        }
+        __syncthreads();  // the slice is stored before the next pre-sieve overwrites it
+    }
+}
+
 int tile_threads(uint32_t tile_log2) { return tile_log2 >= 17 ? 1024 : (tile_log2 >= 14 ? 512 : 256); }
-size_t tile_smem_bytes(uint32_t tile_log2) { return (size_t)1 << (tile_log2 - 3); }
+// a tile (or, beyond 2^20 bits, each CTA's slice of a cluster tile) in shared memory
+size_t tile_smem_bytes(uint32_t tile_log2) { return (size_t)1 << ((tile_log2 < 20 ? tile_log2 : 20) - 3); }
+
+// clusters of two 1024-thread CTAs with a 2^20-bit slice each that fit on the GPU at once
+int ctile_max_clusters()
+{
+    static int cached = 0;
+    if (cached) return cached;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(1024);
+    cfg.gridDim = dim3(2);
+    cfg.dynamicSmemBytes = tile_smem_bytes(20);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_ctile<2>, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    cached = n;
+    return n;
+}
+
+// nclusters clusters of two CTAs; a.run tiles per cluster
+cudaError_t launch_ctiles(const TileArgs &a, uint32_t nclusters, cudaStream_t st)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(1024);
+    cfg.gridDim = dim3(2 * nclusters);
+    cfg.dynamicSmemBytes = tile_smem_bytes(20);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_ctile<2>, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 template <int T>
 static cudaError_t launch_tiles_t(const TileArgs &a, uint32_t grid, cudaStream_t st)
@@ -1262,23 +1504,6 @@ cudaError_t probe_smem_atomics(int nsm, double *atom_per_s)
 // any remote access) and at the end (no remote access after a CTA may exit), reached
 // by every thread of every CTA.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_size()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_barrier()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __global__ void __launch_bounds__(1024, 1) k_probe_dsmem(uint32_t *sink, int peer)
 {
     extern __shared__ uint32_t pm[];
@@ -1352,6 +1577,7 @@ cudaError_t set_kernel_attributes()
     cudaError_t e = cudaFuncSetAttribute(k_tile<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ctile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_scatter_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScSmem);

@@ -312,6 +312,10 @@ int tile_threads(uint32_t tile_log2);
 int tile_blocks_per_sm(uint32_t tile_log2);
 size_t tile_smem_bytes(uint32_t tile_log2);
 cudaError_t launch_tiles(const TileArgs &a, uint32_t grid, cudaStream_t st);
+// tiles of 2^21 bits across clusters of two CTAs (one interval, a.run tiles per cluster)
+constexpr uint32_t kMaxTileLog2 = 21, kClusterTileLog2 = 21;
+int ctile_max_clusters();
+cudaError_t launch_ctiles(const TileArgs &a, uint32_t nclusters, cudaStream_t st);
 constexpr uint32_t kScatterMaxTiles = 1024;  // tiles per scatter unit
 // a scatter unit spans at most 2^30 bits (SUDesc.span), so a unit's entry v = (tile
 // offset << tile_log2) + hit offset stays below 2^31 for every tile size

@@ -129,6 +129,87 @@ def test_tunings_and_ragged_ranges(ctx, tune, j0, nbits):
             S.sieve_set_tuning(ctx, k, **saved[k])
 
 
+# Cluster tiles of 2^21 bits (two CTAs, distributed shared memory).  Intervals of at
+# least 4 tiles per SM keep the tuning's tile size (shorter ones get smaller tiles).
+CLUSTER_TUNINGS = [
+    dict(tile_log2=21, presieve_groups=2, coop_max=4096, medium_max=1 << 21, window_tiles=512, epoch_tiles=2048),
+    dict(tile_log2=21, presieve_groups=4, coop_max=2048, medium_max=1 << 14, window_tiles=64, epoch_tiles=300),
+]
+
+
+def with_tuning(ctx, tune, fn):
+    saved = [S.sieve_get_tuning(ctx, k) for k in range(4)]
+    try:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **tune)
+        return fn()
+    finally:
+        for k in range(4):
+            S.sieve_set_tuning(ctx, k, **saved[k])
+
+
+@pytest.mark.parametrize("tune", CLUSTER_TUNINGS)
+@pytest.mark.parametrize("j0,nbits", [(10**13 // 2 + 96, (1300 << 20) + 224), (10**17 // 2, (1 << 31) + (3 << 19) + 64)])
+def test_cluster_tiles_ragged_ranges(ctx, tune, j0, nbits):
+    def run():
+        out = torch.empty(nbits // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments(ctx, 5, j0 // 32, nbits // 32, out)
+        S.sieve_sync(ctx)
+        return host_words(out)
+    got = with_tuning(ctx, tune, run)
+    want = oracle.sieve_range(j0, nbits)
+    assert first_diff(got, want) is None, first_diff(got, want)
+
+
+def test_config2_cluster_tiles_against_stored_values(ctx):
+    """The 1e15 configuration with 2^21-bit cluster tiles: table hash and segment counts,
+    the host-output path, and the count mode (which runs 2^20-bit tiles) under the
+    same tuning."""
+    l, n = 20, 8192
+    with open(os.path.join(GOLDEN, "c2_segments.txt")) as fh:
+        lines = fh.read().splitlines()
+    want_sha = lines[1].split()[2]
+    want_counts = np.array([int(x.split()[1]) for x in lines[3:]], dtype=np.int64)
+
+    def run():
+        out = torch.empty((n << l) // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments_midpoint(ctx, l, 1, 15, n, out)
+        S.sieve_sync(ctx)
+        words = host_words(out)
+        del out
+        f = S.sieve_f_from_midpoint(l, n, 1, 15)
+        host = torch.empty((n << l) // 32, dtype=torch.int32).pin_memory()
+        S.sieve_segments_host(ctx, l, f, n, host)
+        pr = torch.empty(n, dtype=torch.int64, device="cuda")
+        S.sieve_count_segments(ctx, l, f, n, pr)
+        S.sieve_sync(ctx)
+        return words, host.numpy().view(np.uint32), pr.cpu().numpy()
+    words, hwords, primes = with_tuning(ctx, CLUSTER_TUNINGS[0], run)
+    seg_counts = np.unpackbits(words.view(np.uint8)).reshape(n, -1).sum(axis=1)
+    assert np.array_equal(seg_counts, want_counts)
+    assert sha(words) == want_sha
+    assert sha(hwords) == want_sha
+    assert np.array_equal(primes, (1 << l) - want_counts)
+
+
+def test_config3_cluster_tiles_against_stored_hash(ctx):
+    l, n = 20, 32768
+    f = oracle.f_from_midpoint(l, n, 1 << 60, 0)
+    with open(os.path.join(GOLDEN, "c3_segments.txt")) as fh:
+        want_sha = fh.read().splitlines()[1].split()[2]
+    tune = dict(CLUSTER_TUNINGS[0], medium_max=1 << 20)
+
+    def run():
+        out = torch.empty((n << l) // 32, dtype=torch.int32, device="cuda")
+        S.sieve_segments(ctx, l, f, n, out)
+        S.sieve_sync(ctx)
+        w = host_words(out)
+        del out
+        torch.cuda.empty_cache()
+        return w
+    assert sha(with_tuning(ctx, tune, run)) == want_sha
+
+
 def test_config2_full_table_hash_and_segment_counts(ctx):
     l, n = 20, 8192
     f = oracle.f_from_midpoint(l, n, 1, 15)

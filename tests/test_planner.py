@@ -241,7 +241,7 @@ def test_rejects_bad_arguments(S):
     with pytest.raises(S.SieveError):
         S.sieve_plan_describe(PRIMES, MAX_V, 152, [(1 << 40, 100, 0)], TUNE, records=False)
     with pytest.raises(S.SieveError):
-        S.sieve_plan_describe(PRIMES, MAX_V, 152, ok, dict(TUNE, tile_log2=21), records=False)
+        S.sieve_plan_describe(PRIMES, MAX_V, 152, ok, dict(TUNE, tile_log2=22), records=False)
     with pytest.raises(S.SieveError) as e:
         S.sieve_plan_describe(PRIMES, MAX_V, 152, [(MAX_V, 1 << 20, 0)], TUNE, records=False)
     assert e.value.status == 2
@@ -289,3 +289,18 @@ def test_random_plans_keep_the_invariants(S):
         pool = int(1 << int(rng.integers(12, 32)))
         plan = S.sieve_plan_describe(PRIMES, MAX_V, int(rng.integers(1, 200)), reqs, t, pool_entries=pool)
         check_plan(plan, reqs, t, pool)
+
+
+def test_cluster_tiles_for_one_interval_only(S):
+    """Tiles of 2^21 bits (two-CTA clusters) are planned for a single interval; a batch
+    of several requests takes 2^20-bit tiles under the same tuning."""
+    tune = dict(TUNE, tile_log2=21, window_tiles=512, epoch_tiles=1024)
+    j0, nbits = 10**12, (700 << 21) + 96
+    one = S.sieve_plan_describe(PRIMES, MAX_V, 152, [(j0, nbits, 0)], tune)
+    lens = [t["len"] for t in one["tiles"]]
+    assert max(lens) == 1 << 21 and sum(lens) == nbits and lens[-1] == 96
+    assert all(g["ntiles"] <= 512 for g in one["groups"])
+    two = S.sieve_plan_describe(PRIMES, MAX_V, 152, [(j0, nbits, 0), (j0 + nbits, 1 << 22, nbits // 32)], tune)
+    assert max(t["len"] for t in two["tiles"]) == 1 << 20
+    with pytest.raises(S.SieveError):
+        S.sieve_plan_describe(PRIMES, MAX_V, 152, [(j0, nbits, 0)], dict(tune, window_tiles=1024))  # 2^31-bit units
