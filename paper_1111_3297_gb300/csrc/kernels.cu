@@ -1344,30 +1344,54 @@ __global__ void __launch_bounds__(256) k_goldbach(const uint32_t *__restrict__ b
             const uint64_t left = count - 32 * b;
             valid = alive = left >= 32 ? 0xFFFFFFFFu : (1u << left) - 1u;
             const int64_t hN = (int64_t)((n_lo >> 1) + 32 * b);  // N_0 / 2 (numbers below 2^63)
-            for (uint32_t k = 0; k < nprimes && (alive & ~done); ++k) {
-                const uint32_t p = __ldg(primes + k);
-                const int64_t Jw = hN - (int64_t)((p + 1) >> 1);  // J of N_0 - p
-                const int64_t jw = Jw - (int64_t)j0;               // relative to the table
-                uint32_t w;
-                if (jw >= 0) {
-                    const uint64_t q = (uint64_t)jw >> 5;
-                    const uint32_t lo = __ldg(bits + q);
-                    const uint32_t hi = q + 1 < nwords ? __ldg(bits + q + 1) : 0xFFFFFFFFu;
-                    w = __funnelshift_r(lo, hi, (uint32_t)jw & 31);
-                } else {
-                    // only when the table starts at 1 (j0 = 0): numbers i < -jw have
-                    // N_i - p < 1, and so for every larger p: they fail
-                    if (jw <= -32) break;
-                    const uint32_t sh = (uint32_t)(-jw), below = (1u << sh) - 1u;
-                    w = (__ldg(bits) << sh) | below;
-                    alive &= ~below | done;
+            const int64_t base = hN - (int64_t)j0;               // relative J of N_0 - 1
+            // Away from the table's edges (every block unless the table starts at 1, and
+            // every block but the last): for p = 2q - 1 the window starts at relative
+            // J = base - q, i.e. word (base >> 5) + ((bb - q) >> 5), bit (bb - q) & 31 with
+            // bb = base & 31, all in 32-bit arithmetic.  The host guarantees base - q >= 0
+            // for every p <= p_max when j0 > 0, and the hi word exists except near the end.
+            const bool edges = j0 == 0 || (uint64_t)(base >> 5) + 1 >= nwords;
+            if (!edges) {
+                const uint32_t *row = bits + (base >> 5);
+                const int32_t bb = (int32_t)(base & 31);
+                for (uint32_t k = 0; k < nprimes && (alive & ~done); ++k) {
+                    const uint32_t p = __ldg(primes + k);
+                    const int32_t t = bb - (int32_t)((p + 1) >> 1);
+                    const uint32_t *r = row + (t >> 5);  // arithmetic shift: floor division
+                    const uint32_t w = __funnelshift_r(__ldg(r), __ldg(r + 1), (uint32_t)t & 31);
+                    const uint32_t prime = ~w & alive & ~done;
+                    if (prime) {
+                        done |= prime;
+                        p_last = p;
+                        first_last = __ffs(prime) - 1;
+                    }
                 }
-                uint32_t prime = ~w & alive & ~done;
-                if (Jw <= 0 && Jw > -32) prime &= ~(1u << (uint32_t)(-Jw));  // N_i - p = 1
-                if (prime) {
-                    done |= prime;
-                    p_last = p;
-                    first_last = __ffs(prime) - 1;
+            } else {
+                for (uint32_t k = 0; k < nprimes && (alive & ~done); ++k) {
+                    const uint32_t p = __ldg(primes + k);
+                    const int64_t Jw = hN - (int64_t)((p + 1) >> 1);  // J of N_0 - p
+                    const int64_t jw = Jw - (int64_t)j0;               // relative to the table
+                    uint32_t w;
+                    if (jw >= 0) {
+                        const uint64_t q = (uint64_t)jw >> 5;
+                        const uint32_t lo = __ldg(bits + q);
+                        const uint32_t hi = q + 1 < nwords ? __ldg(bits + q + 1) : 0xFFFFFFFFu;
+                        w = __funnelshift_r(lo, hi, (uint32_t)jw & 31);
+                    } else {
+                        // only when the table starts at 1 (j0 = 0): numbers i < -jw have
+                        // N_i - p < 1, and so for every larger p: they fail
+                        if (jw <= -32) break;
+                        const uint32_t sh = (uint32_t)(-jw), below = (1u << sh) - 1u;
+                        w = (__ldg(bits) << sh) | below;
+                        alive &= ~below | done;
+                    }
+                    uint32_t prime = ~w & alive & ~done;
+                    if (Jw <= 0 && Jw > -32) prime &= ~(1u << (uint32_t)(-Jw));  // N_i - p = 1
+                    if (prime) {
+                        done |= prime;
+                        p_last = p;
+                        first_last = __ffs(prime) - 1;
+                    }
                 }
             }
         }
