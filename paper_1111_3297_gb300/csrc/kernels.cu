@@ -1052,12 +1052,15 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         // the lane group's prime and state (one prime per lane)
         uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0, gwi = 0;
         uint64_t h = 0;
-        // the next lane group's words, loaded ahead
+        // the next lane group's words, loaded ahead: its prime and either its state
+        // word or, in the interval's first group, its Barrett constant (the primes are
+        // padded past the chunk, the constants are not)
         uint32_t p_n = 0;
         unsigned long long w_n = 0;
         if (lg < nlg) {
-            p_n = pr[lg * 32 + lane];
-            if (!first) w_n = stw[lg * 32 + lane];
+            const uint32_t ni = lg * 32 + lane;
+            p_n = pr[ni];
+            w_n = !first ? stw[ni] : (ni < n ? pm[ni] : 0ull);
         }
         bool need = true;
         for (;;) {
@@ -1070,16 +1073,17 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                     const unsigned long long w = w_n;
                     const uint32_t nl = lg + kScNW;
                     if (nl < nlg) {
-                        p_n = pr[nl * 32 + lane];
-                        if (!first) w_n = stw[nl * 32 + lane];
+                        const uint32_t ni = nl * 32 + lane;
+                        p_n = pr[ni];
+                        w_n = !first ? stw[ni] : (ni < n ? pm[ni] : 0ull);
                     }
                     h = kRunInf;
                     s = 0;
                     if (idx < n) {
                         if (first) {
                             if (p <= u.plimit) {
-                                const uint64_t hh = BIG ? first_hit_big(u.J, jsx, p, pm[idx], a.wheel, s)
-                                                        : first_hit(u.J, jsx, p, pm[idx], s);
+                                const uint64_t hh = BIG ? first_hit_big(u.J, jsx, p, w, a.wheel, s)
+                                                        : first_hit(u.J, jsx, p, w, s);
                                 h = hh < kRunInf ? hh : kRunInf;
                             }
                         } else {
