@@ -215,7 +215,10 @@ sieve_status sieve_batch(sieve_ctx *ctx, const sieve_req *host_reqs, uint32_t co
 /*
  * Tuning of the device path (none of it changes the bits); sieve_set_tuning
  * returns SIEVE_EINVAL outside these ranges:
- *   tile_log2     on-chip segment size 2^tile_log2 bits (12..20), one CTA per tile;
+ *   tile_log2     on-chip segment size 2^tile_log2 bits (12..21), one CTA per tile up
+ *                 to 2^20; 21 holds a segment across a cluster of two CTAs (distributed
+ *                 shared memory, one interval only: batches, servers and the count
+ *                 mode take 2^20; measured slower than 20 on GB300, hence opt-in);
  *   presieve_groups  how many small-prime pattern groups pre-sieve a tile
  *                 (1..13; group 1 = {3,5,7,11,13}, up to 127 with 13 groups);
  *   coop_max      primes up to this are struck by a whole warp, 32 multiples at a
