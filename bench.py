@@ -460,7 +460,9 @@ def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_
     step_roof["t_hbm_impl_ms"] = b_impl / (hbm_peak * 1e9) * 1e3
     return {"N": N, "ms": ms_max, "steps": steps, "value_local": N * steps / (ms * 1e-3),
             "ms_max": ms_max, "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
-            "clocks": clk, "launches": int(sum(prof["launches"])), "out": out}
+            # kernels of the library inside the timed region: each tile and scatter launch,
+            # plus the per-tile hit sum (k_sum_u32) that profiling runs after each scatter
+            "clocks": clk, "launches": int(sum(prof["launches"]) + prof["launches"][S.K_SCATTER]), "out": out}
 
 
 def measure_fresh(S, ctx, l, f, n, steps, host=False):
