@@ -370,7 +370,8 @@ def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_
     `warmup` untimed calls, CUDA events on the launching stream around the whole
     timed region, nvidia-smi clocks sampled during it.  Returns the device-timed
     figures with the per-kernel split, the dominant kernel's roofline and the step
-    roofline (the north-star definition), and keeps the table in ["out"]."""
+    roofline (the slower of the algorithmic HBM bytes at the copy bandwidth and the marks at
+    the shared-atomic rate, over the step time), and keeps the table in ["out"]."""
     import torch
     N = n << l
     J0 = f << l
@@ -453,7 +454,7 @@ def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_
                 "frac": ach / hbm_peak, "traffic": traffic["k_scatter"],
                 "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
     step_roof = step_roofline(N, marks, h_large, visits, ms_max * 1e-3 / steps, hbm_peak, r_atom)
-    # beside the benchmark spec's figure (16 B per hit: the paper's (p, q) pair written and
+    # beside the step roofline's byte count (16 B per hit: the paper's (p, q) pair written and
     # read), the bytes this design moves: 4-byte bucket entries written and read
     b_impl = N / 8 + 8 * h_large + 20 * visits
     step_roof["bytes_impl"] = b_impl
