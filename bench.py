@@ -567,6 +567,54 @@ def measure_consumers(S, ctx, l, f, n, steps):
     return {"count": count, "goldbach": gold}
 
 
+def measure_stream(S, ctx, hbm_peak, r_atom, k=8):
+    """A long range sieved as k consecutive intervals of 2^30 bits (l = 20, n = 1024), the
+    paper's segment-after-segment mode, at 1e15 and 1e18: with streaming on, each interval
+    continues from the previous one's large-prime state (no first hits for them); off,
+    every interval computes them.  Plans are built in an untimed first pass; then the k
+    intervals are timed with CUDA events (the first of them starts a new chain), with the
+    step roofline of the streamed form."""
+    import torch
+    l, n = 20, 1024
+    N = n << l
+    out = torch.empty(N // 32, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for e in (15, 18):
+        f0 = S.sieve_f_from_midpoint(l, n, 1, e)
+        row = {}
+        for mode in ("off", "on"):
+            S.sieve_set_streaming(ctx, mode == "on")
+            for j in range(k):
+                S.sieve_segments(ctx, l, f0 + j * n, n, out)
+            S.sieve_sync(ctx)
+            S.sieve_profile_enable(ctx, mode == "on")
+            S.sieve_profile_read(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for j in range(k):
+                S.sieve_segments(ctx, l, f0 + j * n, n, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = S.sieve_profile_read(ctx)
+            S.sieve_profile_enable(ctx, False)
+            S.sieve_sync(ctx)
+            t = e0.elapsed_time(e1) * 1e-3 / k
+            row[mode] = {"ms": t * 1e3, "value": N / t}
+            if mode == "on":
+                J0 = f0 << l
+                tune = S.sieve_get_tuning(ctx, 1 if e == 15 else 3)
+                h_large = prof["large_hits"] / k
+                roof = step_roofline(N, medium_marks(J0, N, tune) + h_large, h_large, prof["prime_reads"] / k, t,
+                                     hbm_peak, r_atom)
+                row["on"]["step_roofline_frac"] = roof["frac"]
+                row["on"]["continued_primes_per_interval"] = prof["continued"] / k
+        S.sieve_set_streaming(ctx, False)
+        res["1e%d" % e] = row
+    del out
+    return {"l": l, "n": n, "intervals": k, "unit": "odd numbers/s", "points": res}
+
+
 def measure_batch(S, ctx, args, rank, world, hbm_peak, r_atom):
     """args.batch_requests (4096) seeded requests of uneven length (2^16..2^28 numbers) and magnitude
     (1e6..1e18): the batched form (one graph-replayed launch sequence) against the
@@ -826,8 +874,10 @@ def main():
         consumers = measure_consumers(S, ctx, l, f, n, max(2, min(args.steps, 5)))
 
     sweep = None
+    streamed = None
     if rank == 0 and not args.no_sweep:
         sweep = measure_sweep(S, ctx, hbm_peak, r_atom)
+        streamed = measure_stream(S, ctx, hbm_peak, r_atom)
 
     base_line = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -851,7 +901,7 @@ def main():
             "gpu_launches": m["launches"],
             "roofline": m["roofline"], "step_roofline": m["step_roofline"], "kernels": m["kernels"],
             "cpu_baseline": base_line, "e2e": e2e, "fresh": fresh, "clocks": m["clocks"],
-            "c3": c3, "consumers": consumers, "batch": batch, "serving": serving, "sweep": sweep,
+            "c3": c3, "consumers": consumers, "streaming": streamed, "batch": batch, "serving": serving, "sweep": sweep,
             "composites": composites, "smem_atomic_peak_per_s": r_atom, "dsmem_probe": dsmem,
         }), flush=True)
     ctx.close()

@@ -187,6 +187,23 @@ sieve_status sieve_count(sieve_ctx *ctx, const uint32_t *dev_bits, uint64_t nbit
 sieve_status sieve_count_noalloc(const uint32_t *dev_bits, uint64_t nbits, uint64_t *dev_count,
                                  sieve_stream stream);
 
+/*
+ * Streaming of consecutive intervals (enable = 1; 0 turns it off).  A long range sieved
+ * as consecutive calls of sieve_segments (or sieve_segments_host, sieve_count_segments),
+ * each starting where the previous one ended, is the paper's own mode of work (Sec. 2.4:
+ * segments in order, each large prime's next hit carried along, Sec. 2.3).  With
+ * streaming on, every single-interval call keeps its large primes' next hits after its
+ * last segment in the context, and a call that starts exactly where the previous one
+ * ended, with the same tuning class choices (large-prime bound and wheel), continues
+ * from them instead of computing each large prime's first hit again; primes the new
+ * interval adds take first hits as usual.  The bits are the same either way.  Any other
+ * call that runs device work on the context (a batch, an interval elsewhere, a tuning
+ * run) ends the continuation; so does turning streaming on or off.  Calls must come in
+ * order on one stream (or be ordered by the caller).  While streaming is on, single
+ * intervals run without CUDA-graph replay.
+ */
+sieve_status sieve_set_streaming(sieve_ctx *ctx, int enable);
+
 /* Wait for `stream` and report any device-side error recorded since the last wait. */
 sieve_status sieve_sync(sieve_ctx *ctx, sieve_stream stream);
 
@@ -291,6 +308,8 @@ typedef struct {
     uint64_t large_hits;     /* bucket entries emitted (large-prime hits) */
     uint64_t medium_marks;   /* estimated in-tile marks by medium primes */
     uint64_t prime_reads;    /* (prime, scatter unit) visits in the scatter */
+    uint64_t continued;      /* large primes that continued from the previous interval's
+                                state instead of taking a first hit (streaming) */
 } sieve_profile;
 #define SIEVE_K_TILE 0
 #define SIEVE_K_SCATTER 1

@@ -646,6 +646,10 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     // profiling covers the context's own plans, not server lanes (their own scratch,
     // enqueued from the server's thread)
     const bool prof = c->prof && &scr == &c->scr;
+    // streaming: continue from the previous interval's state words, and keep this one's
+    const bool own = &scr == &c->scr;
+    const bool stream_this = own && c->stream_plan == P;
+    const uint32_t first_from = stream_this ? c->stream_first_from : 0u;
     cudaStream_t st = scr.s_tile, ss = prof && c->prof_serial ? scr.s_tile : scr.s_scat;
     CK(cudaEventRecord(scr.ev_fork, ls));
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
@@ -679,7 +683,8 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             sa.state = scr.d_carry;
             sa.state_base = P->state_base;
             sa.run_first = run_first ? 1u : 0u;
-            sa.run_last = ei == last_scatter ? 1u : 0u;
+            sa.run_last = ei == last_scatter && !stream_this ? 1u : 0u;
+            sa.first_from = first_from;
             run_first = false;
             sa.wheel.gapw = c->d_gapw;
             sa.wheel.rstate = c->d_rstate;
@@ -771,10 +776,27 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     CK(cudaStreamWaitEvent(st, scr.ev_join, 0));
     CK(cudaEventRecord(scr.ev_join, st));
     CK(cudaStreamWaitEvent(ls, scr.ev_join, 0));
+    if (own) {
+        // every plan on the context's scratch may overwrite the state words
+        ++c->carry_gen;
+        if (stream_this) {
+            const TileDesc &tl = P->tiles.back();
+            c->cont.valid = true;
+            c->cont.next_J = tl.J + tl.len;
+            c->cont.p_lo = P->groups[0].p_lo;
+            c->cont.p_hi = P->groups[0].p_hi;
+            c->cont.big_wheel = P->big_wheel;
+            c->cont.gen = c->carry_gen;
+            c->cont.scr_gen = scr.gen;
+        } else {
+            c->cont.valid = false;
+        }
+    }
     if (prof) {
         c->prof_acc.tiles += P->tiles.size();
         c->prof_acc.bits += P->bits;
         for (const auto &g : P->groups) c->prof_acc.prime_reads += (uint64_t)(g.p_hi - g.p_lo) * g.nsu;
+        c->prof_acc.continued += first_from;
     }
     return SIEVE_OK;
 }
@@ -792,8 +814,12 @@ sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long
     // every plan of the context shares its scratch (bucket pools, counters), so its
     // work starts after the previous plan's, whichever streams the two were issued on
     CK(cudaStreamWaitEvent(st, c->ev_last, 0));
-    const bool graph = allow_graph && !c->prof;
+    // streaming runs one interval after another, each plan once: no graphs
+    const bool streamed = c->streaming && P->run_scatter;
+    const bool graph = allow_graph && !c->prof && !streamed;
     if (graph && P->exec && P->g_out == out && P->g_counts == counts && P->g_gen == c->scr.gen) {
+        ++c->carry_gen;  // the replay may overwrite the state words
+        c->cont.valid = false;
         CK(cudaGraphLaunch(P->exec, st));
         CK(cudaEventRecord(c->ev_last, st));
         P->runs++;
@@ -822,7 +848,19 @@ sieve_status run_plan_n(sieve_ctx *c, Plan *P, uint32_t *out, unsigned long long
         P->runs++;
         return SIEVE_OK;
     }
+    c->stream_plan = nullptr;
+    if (streamed) {
+        // continue where the previous interval ended: same large primes and wheel, and its
+        // state words untouched since
+        const GroupDesc &G0 = P->groups[0];
+        const bool ok = c->cont.valid && c->cont.gen == c->carry_gen && c->cont.scr_gen == c->scr.gen &&
+                        P->tiles[0].J == c->cont.next_J && G0.p_lo == c->cont.p_lo &&
+                        P->big_wheel == c->cont.big_wheel;
+        c->stream_plan = P;
+        c->stream_first_from = ok ? std::min(c->cont.p_hi, G0.p_hi) - G0.p_lo : 0u;
+    }
     s = enqueue_plan(c, c->scr, P, out, counts, ncounts, st);
+    c->stream_plan = nullptr;
     if (!s) CK(cudaEventRecord(c->ev_last, st));
     P->runs++;
     return s;
@@ -1498,5 +1536,13 @@ sieve_status sieve_probe_dsmem_atomics(int device, uint32_t cluster_size, int pe
         return SIEVE_EINVAL;
     CK(cudaSetDevice(device));
     CK(probe_dsmem_atomics(cluster_size, peer ? 1 : 0, atomics_per_s, ctas));
+    return SIEVE_OK;
+}
+
+sieve_status sieve_set_streaming(sieve_ctx *c, int enable)
+{
+    if (!c) return SIEVE_EINVAL;
+    c->streaming = enable != 0;
+    c->cont.valid = false;
     return SIEVE_OK;
 }

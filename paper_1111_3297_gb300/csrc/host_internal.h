@@ -151,6 +151,21 @@ struct sieve_ctx {
     std::vector<gbs::ProfRec> prof_recs;
     sieve_profile prof_acc{};
     int sticky_err = 0;
+    // streaming (sieve_set_streaming): the large-prime state words of the last single
+    // interval, valid for an interval that starts where it ended while no other plan on
+    // the context's scratch has run since (carry_gen counts those runs)
+    bool streaming = false;
+    struct Continuation {
+        bool valid = false;
+        uint64_t next_J = 0;        // the first bit after the interval
+        uint32_t p_lo = 0, p_hi = 0; // large primes whose state words hold their next hits
+        bool big_wheel = false;
+        uint64_t gen = 0;
+        uint64_t scr_gen = 0;        // the scratch's buffers have not moved since
+    } cont;
+    uint64_t carry_gen = 0;
+    const gbs::Plan *stream_plan = nullptr;  // the plan run_plan_n enqueues in streaming mode
+    uint32_t stream_first_from = 0;          // its primes with state words (from p_lo)
 };
 
 namespace gbs {

@@ -1053,14 +1053,16 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         uint32_t lg = warp, p = 0, s = 0, gw = 0, idx = 0, gwi = 0;
         uint64_t h = 0;
         // the next lane group's words, loaded ahead: its prime and either its state
-        // word or, in the interval's first group, its Barrett constant (the primes are
-        // padded past the chunk, the constants are not)
+        // word or, for a prime that takes a first hit in the interval's first group, its
+        // Barrett constant (the primes are padded past the chunk, the constants are not)
+        const uint32_t rel0 = ch.p_lo - a.state_base;  // index of the chunk's first prime in the state
+        auto fresh = [&](uint32_t i) { return first && rel0 + i >= a.first_from; };
         uint32_t p_n = 0;
         unsigned long long w_n = 0;
         if (lg < nlg) {
             const uint32_t ni = lg * 32 + lane;
             p_n = pr[ni];
-            w_n = !first ? stw[ni] : (ni < n ? pm[ni] : 0ull);
+            w_n = !fresh(ni) ? stw[ni] : (ni < n ? pm[ni] : 0ull);
         }
         bool need = true;
         for (;;) {
@@ -1075,12 +1077,12 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                     if (nl < nlg) {
                         const uint32_t ni = nl * 32 + lane;
                         p_n = pr[ni];
-                        w_n = !first ? stw[ni] : (ni < n ? pm[ni] : 0ull);
+                        w_n = !fresh(ni) ? stw[ni] : (ni < n ? pm[ni] : 0ull);
                     }
                     h = kRunInf;
                     s = 0;
                     if (idx < n) {
-                        if (first) {
+                        if (fresh(idx)) {
                             if (p <= u.plimit) {
                                 const uint64_t hh = BIG ? first_hit_big(u.J, jsx, p, w, a.wheel, s)
                                                         : first_hit(u.J, jsx, p, w, s);

@@ -297,6 +297,9 @@ struct ScatterArgs {
     uint32_t state_base;
     uint32_t run_first;
     uint32_t run_last;              // 1 when the launch's last group is the interval's last (no state after it)
+    uint32_t first_from;            // with run_first: primes (index - state_base) below this continue
+                                    // from their state words (the previous interval ended where this
+                                    // one starts); the others take a first hit
     BigWheel wheel;
     uint32_t *bkt;
     uint32_t *bkt_cnt;

@@ -44,7 +44,7 @@ class Req(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", _u64 * 8), ("ms", _dbl * 8), ("tiles", _u64), ("bits", _u64),
-                ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64)]
+                ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64), ("continued", _u64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -98,6 +98,7 @@ def lib():
             "sieve_goldbach": (_i32, [_vp, _vp, _u64, _u64, _u64, _u64, _u32, _u32, _vp, _vp]),
             "sieve_count": (_i32, [_vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "sieve_sync": (_i32, [_vp, _vp]),
+            "sieve_set_streaming": (_i32, [_vp, _i32]),
             "sieve_batch": (_i32, [_vp, ctypes.POINTER(Req), _u32, _vp, _vp, _vp]),
             "sieve_get_tuning": (_i32, [_vp, _u32, ctypes.POINTER(Tuning)]),
             "sieve_set_tuning": (_i32, [_vp, _u32, ctypes.POINTER(Tuning)]),
@@ -267,6 +268,11 @@ def sieve_count(ctx, dev_bits, nbits, stream=None):
     return out.value
 
 
+def sieve_set_streaming(ctx, enable=True):
+    """Consecutive single-interval calls continue from each other's large-prime state."""
+    _check(lib().sieve_set_streaming(ctx.handle, 1 if enable else 0), "sieve_set_streaming")
+
+
 def sieve_sync(ctx, stream=None):
     _check(lib().sieve_sync(ctx.handle, _stream(stream)), "sieve_sync")
 
@@ -330,7 +336,8 @@ def sieve_profile_read(ctx, stream=None):
     p = Profile()
     _check(lib().sieve_profile_read(ctx.handle, ctypes.byref(p), _stream(stream)), "sieve_profile_read")
     return {"launches": list(p.launches), "ms": list(p.ms), "tiles": p.tiles, "bits": p.bits,
-            "large_hits": p.large_hits, "medium_marks": p.medium_marks, "prime_reads": p.prime_reads}
+            "large_hits": p.large_hits, "medium_marks": p.medium_marks, "prime_reads": p.prime_reads,
+            "continued": p.continued}
 
 
 def sieve_probe_smem_atomics(device=0):
