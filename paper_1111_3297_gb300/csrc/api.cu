@@ -650,6 +650,12 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     const bool own = &scr == &c->scr;
     const bool stream_this = own && c->stream_plan == P;
     const uint32_t first_from = stream_this ? c->stream_first_from : 0u;
+    if (own) {
+        // this plan may overwrite the state words: no continuation survives it unless it
+        // is enqueued in full as a streamed interval (recorded at the end)
+        ++c->carry_gen;
+        c->cont.valid = false;
+    }
     cudaStream_t st = scr.s_tile, ss = prof && c->prof_serial ? scr.s_tile : scr.s_scat;
     CK(cudaEventRecord(scr.ev_fork, ls));
     CK(cudaStreamWaitEvent(st, scr.ev_fork, 0));
@@ -777,8 +783,6 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
     CK(cudaEventRecord(scr.ev_join, st));
     CK(cudaStreamWaitEvent(ls, scr.ev_join, 0));
     if (own) {
-        // every plan on the context's scratch may overwrite the state words
-        ++c->carry_gen;
         if (stream_this) {
             const TileDesc &tl = P->tiles.back();
             c->cont.valid = true;
@@ -788,8 +792,6 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
             c->cont.big_wheel = P->big_wheel;
             c->cont.gen = c->carry_gen;
             c->cont.scr_gen = scr.gen;
-        } else {
-            c->cont.valid = false;
         }
     }
     if (prof) {
