@@ -788,7 +788,9 @@ def main():
     # the batch and serving legs draw requests up to ~1e18, the Goldbach leg works just
     # above 1e18, the 2^60 sub-record sieves up to 2^60 + 2^35
     wide = not (args.no_batch and args.no_serve and args.no_sweep and args.no_consumers) or c3_on
-    ctx = S.sieve_init(local, max_v=max(vmax, 2 * 10**18 + (1 << 31)) if wide else vmax)
+    # the fresh-interval legs sieve the next 2 * fresh_steps intervals after this rank's
+    vmax_fresh = 2 * ((f0 + world * n + 2 * (args.fresh_steps + 1) * n) << l)
+    ctx = S.sieve_init(local, max_v=max(vmax_fresh, 2 * 10**18 + (1 << 31)) if wide else vmax_fresh)
 
     tuned = None
     if args.tuning:
