@@ -1055,14 +1055,24 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         // the next lane group's words, loaded ahead: its prime and either its state
         // word or, for a prime that takes a first hit in the interval's first group, its
         // Barrett constant (the primes are padded past the chunk, the constants are not)
+        // Whether the chunk's primes take first hits is decided per chunk (a warp-uniform
+        // choice of one load); only the chunk that straddles a streamed interval's
+        // boundary decides per prime.
         const uint32_t rel0 = ch.p_lo - a.state_base;  // index of the chunk's first prime in the state
-        auto fresh = [&](uint32_t i) { return first && rel0 + i >= a.first_from; };
+        const bool all_fresh = first && rel0 >= a.first_from;
+        const bool mixed = first && !all_fresh && rel0 + n > a.first_from;
+        auto fresh = [&](uint32_t i) { return all_fresh || (mixed && rel0 + i >= a.first_from); };
+        auto next_word = [&](uint32_t i) -> unsigned long long {
+            if (all_fresh) return i < n ? pm[i] : 0ull;
+            if (!mixed) return stw[i];
+            return rel0 + i >= a.first_from ? (i < n ? pm[i] : 0ull) : stw[i];
+        };
         uint32_t p_n = 0;
         unsigned long long w_n = 0;
         if (lg < nlg) {
             const uint32_t ni = lg * 32 + lane;
             p_n = pr[ni];
-            w_n = !fresh(ni) ? stw[ni] : (ni < n ? pm[ni] : 0ull);
+            w_n = next_word(ni);
         }
         bool need = true;
         for (;;) {
@@ -1077,7 +1087,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                     if (nl < nlg) {
                         const uint32_t ni = nl * 32 + lane;
                         p_n = pr[ni];
-                        w_n = !fresh(ni) ? stw[ni] : (ni < n ? pm[ni] : 0ull);
+                        w_n = next_word(ni);
                     }
                     h = kRunInf;
                     s = 0;
