@@ -181,8 +181,9 @@ try {
             std::lock_guard<std::mutex> g(mu);
             got = arena.alloc(2 * pool_bytes(entries), &off);
             if (!got) {
+                // pools of `fit` entries take pool_bytes(fit) <= half bytes each (granule included)
                 const uint64_t half = arena.largest() / 2 / kGranule * kGranule;
-                const uint64_t fit = half >= 64 + 4 * kMinPoolEntries ? ((half - 64) / 4) & ~3ull : 0;
+                const uint64_t fit = half >= 64 + kGranule + 4 * kMinPoolEntries ? ((half - 64 - kGranule) / 4) & ~3ull : 0;
                 if (fit >= kMinPoolEntries && (fit >= max_cap || !others_busy)) {
                     entries = fit;
                     got = arena.alloc(2 * pool_bytes(entries), &off);
