@@ -86,3 +86,15 @@ def test_goldbach_argument_errors(ctx):
         S.sieve_goldbach(ctx, out, 0, 4 << 12, 4, (1 << 14) + 2, 100, 12, w)  # N - 3 beyond the table
     with pytest.raises(S.SieveError):
         S.sieve_goldbach(ctx, out, 64, 4 << 12, 100, 16, 101, 5, w)    # N - p_max below the table
+
+
+@pytest.mark.parametrize("n_lo,count,win", [(4, 1, 5), (6, 3, 32), (1000, 33, 5), (4, 1 << 20, 32)])
+def test_goldbach_edge_ranges(ctx, n_lo, count, win):
+    # tables from 1: one number, a window wider than the range, a block straddling two
+    # windows of 32, a 2^32-number window over 2^20 numbers
+    l, f = 12, 0
+    n = ((n_lo + 2 * count) // 2 >> l) + 1
+    out = table(ctx, l, f, n)
+    got = device_windows(ctx, out, 0, n << l, n_lo, count, 997, win)
+    want = oracle.goldbach_windows(n_lo, oracle.goldbach_min_p(n_lo, count, 997), win)
+    assert got == want
