@@ -28,6 +28,8 @@ WORKLOADS = {
     "c2": dict(name="l20_n8192_mid1e15", l=20, n=8192, mant=1, exp10=15),
     "c3": dict(name="l20_n32768_mid2p60", l=20, n=32768, mant=1 << 60, exp10=0),
     "c1": dict(name="l15_f0_n1024", l=15, n=1024, f=0),
+    # one point of the paper's Table 1 sweep: 2^30 odd numbers around 10^18 (profiling case)
+    "m1e18": dict(name="l20_n1024_mid1e18", l=20, n=1024, mant=1, exp10=18),
 }
 
 
@@ -37,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "m1e18"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="JSON tuning to use as is (no autotune), e.g. for profiling")
     ap.add_argument("--no-e2e", action="store_true")
