@@ -418,22 +418,24 @@ def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_
     h_medium = medium_marks(J0, N, tune)  # per step
     h_large = prof["large_hits"] / steps
     visits = prof["prime_reads"] / steps
+    state_writes = prof["state_writes"] / steps
     t_tile = prof["ms"][S.K_TILE] / steps * 1e-3
     t_scatter = prof["ms"][S.K_SCATTER] / steps * 1e-3
     n_tile = prof["launches"][S.K_TILE] / steps
     n_scatter = prof["launches"][S.K_SCATTER] / steps
     marks = h_medium + h_large
     # tile: table written once, each bucket entry read once; scatter (one interval):
-    # each bucket entry written once, and per prime and scatter group the prime (4 B)
-    # and its 8-byte state word read and written back
+    # each bucket entry written once; per prime and scatter group the prime (4 B) and an
+    # 8-byte word read (its Barrett constant in the first group, else its state word);
+    # the 8-byte state words the library counted as written back
     tile_bytes = N / 8 + 4 * h_large
-    scatter_bytes = 4 * h_large + 20 * visits
+    scatter_bytes = 4 * h_large + 12 * visits + 8 * state_writes
     kernels = {
         "k_tile": {"ms_per_step": t_tile * 1e3, "launches_per_step": n_tile,
                    "marks": marks, "atomics_per_s": marks / t_tile if t_tile else None,
                    "hbm_bytes": tile_bytes, "hbm_gbs": tile_bytes / t_tile / 1e9 if t_tile else None},
         "k_scatter": {"ms_per_step": t_scatter * 1e3, "launches_per_step": n_scatter,
-                      "hits": h_large, "visits": visits, "hbm_bytes": scatter_bytes,
+                      "hits": h_large, "visits": visits, "state_writes": state_writes, "hbm_bytes": scatter_bytes,
                       "hbm_gbs": scatter_bytes / t_scatter / 1e9 if t_scatter else None},
     }
     traffic = load_traffic(traffic_key, N, h_large, n_tile, n_scatter)
@@ -458,7 +460,7 @@ def measure_interval(S, ctx, l, f, n, steps, warmup, tune, hbm_peak, hbm_src, r_
     step_roof = step_roofline(N, marks, h_large, visits, ms_max * 1e-3 / steps, hbm_peak, r_atom)
     # beside the step roofline's byte count (16 B per hit: the paper's (p, q) pair written and
     # read), the bytes this design moves: 4-byte bucket entries written and read
-    b_impl = N / 8 + 8 * h_large + 20 * visits
+    b_impl = N / 8 + 8 * h_large + 12 * visits + 8 * state_writes
     step_roof["bytes_impl"] = b_impl
     step_roof["t_hbm_impl_ms"] = b_impl / (hbm_peak * 1e9) * 1e3
     return {"N": N, "ms": ms_max, "steps": steps, "value_local": N * steps / (ms * 1e-3),
@@ -818,7 +820,7 @@ def main():
     tune = tuned or S.sieve_get_tuning(ctx, cls)
 
     m = measure_interval(S, ctx, l, f, n, args.steps, args.warmup, tune, hbm_peak, hbm_src, r_atom,
-                         {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60"}.get(args.workload), pg,
+                         {"c2": "l20_n1024_mid1e15", "c3": "l20_n4096_mid2p60", "m1e18": "l20_n1024_mid1e18"}.get(args.workload), pg,
                          args.clocks_csv)
     out = m.pop("out")
     ms_max = m["ms_max"]

@@ -310,6 +310,9 @@ typedef struct {
     uint64_t prime_reads;    /* (prime, scatter unit) visits in the scatter */
     uint64_t continued;      /* large primes that continued from the previous interval's
                                 state instead of taking a first hit (streaming) */
+    uint64_t state_writes;   /* 8-byte state words the single-interval scatter wrote back:
+                                one per prime and scatter group, except in the interval's
+                                last group when the interval is not streamed */
 } sieve_profile;
 #define SIEVE_K_TILE 0
 #define SIEVE_K_SCATTER 1

@@ -799,6 +799,15 @@ sieve_status enqueue_plan(sieve_ctx *c, Scratch &scr, Plan *P, uint32_t *out, un
         c->prof_acc.bits += P->bits;
         for (const auto &g : P->groups) c->prof_acc.prime_reads += (uint64_t)(g.p_hi - g.p_lo) * g.nsu;
         c->prof_acc.continued += first_from;
+        if (P->run_scatter) {
+            // the single-interval scatter writes every group's state words back but those of
+            // the interval's last group, unless the interval is streamed
+            size_t last = P->groups.size();
+            for (size_t ei = 0; ei < P->epochs.size(); ++ei)
+                if (P->epochs[ei].ng) last = P->epochs[ei].g0 + P->epochs[ei].ng - 1;
+            for (size_t gi = 0; gi < P->groups.size(); ++gi)
+                if (gi != last || stream_this) c->prof_acc.state_writes += P->groups[gi].p_hi - P->groups[gi].p_lo;
+        }
     }
     return SIEVE_OK;
 }

@@ -1022,6 +1022,22 @@ __device__ __forceinline__ uint32_t big_wheel_pos(uint32_t gw, uint32_t gwi)
     return 8 * gwi + 8 - ((32 - __clz(gw) + 3) >> 2);
 }
 
+// Loads of words read once per launch (a chunk's primes, Barrett constants and state
+// words), marked not to allocate in L1: the L1 then keeps what is read again and again,
+// the mod-15015 wheel tables of the first hits and the gap words of the emission.
+__device__ __forceinline__ uint32_t ld_no_l1_alloc_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_no_l1_alloc_u64(const void *p)
+{
+    unsigned long long v;
+    asm volatile("ld.global.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
 template <bool BIG>
 __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
 {
@@ -1063,15 +1079,16 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
         const bool mixed = first && !all_fresh && rel0 + n > a.first_from;
         auto fresh = [&](uint32_t i) { return all_fresh || (mixed && rel0 + i >= a.first_from); };
         auto next_word = [&](uint32_t i) -> unsigned long long {
-            if (all_fresh) return i < n ? pm[i] : 0ull;
-            if (!mixed) return stw[i];
-            return rel0 + i >= a.first_from ? (i < n ? pm[i] : 0ull) : stw[i];
+            if (all_fresh) return i < n ? ld_no_l1_alloc_u64(pm + i) : 0ull;
+            if (!mixed) return ld_no_l1_alloc_u64(stw + i);
+            return rel0 + i >= a.first_from ? (i < n ? ld_no_l1_alloc_u64(pm + i) : 0ull)
+                                            : ld_no_l1_alloc_u64(stw + i);
         };
         uint32_t p_n = 0;
         unsigned long long w_n = 0;
         if (lg < nlg) {
             const uint32_t ni = lg * 32 + lane;
-            p_n = pr[ni];
+            p_n = ld_no_l1_alloc_u32(pr + ni);
             w_n = next_word(ni);
         }
         bool need = true;
@@ -1086,7 +1103,7 @@ __global__ void __launch_bounds__(kScT, 2) k_scatter_run(ScatterArgs a)
                     const uint32_t nl = lg + kScNW;
                     if (nl < nlg) {
                         const uint32_t ni = nl * 32 + lane;
-                        p_n = pr[ni];
+                        p_n = ld_no_l1_alloc_u32(pr + ni);
                         w_n = next_word(ni);
                     }
                     h = kRunInf;

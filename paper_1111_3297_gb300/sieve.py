@@ -44,7 +44,8 @@ class Req(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", _u64 * 8), ("ms", _dbl * 8), ("tiles", _u64), ("bits", _u64),
-                ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64), ("continued", _u64)]
+                ("large_hits", _u64), ("medium_marks", _u64), ("prime_reads", _u64), ("continued", _u64),
+                ("state_writes", _u64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -337,7 +338,7 @@ def sieve_profile_read(ctx, stream=None):
     _check(lib().sieve_profile_read(ctx.handle, ctypes.byref(p), _stream(stream)), "sieve_profile_read")
     return {"launches": list(p.launches), "ms": list(p.ms), "tiles": p.tiles, "bits": p.bits,
             "large_hits": p.large_hits, "medium_marks": p.medium_marks, "prime_reads": p.prime_reads,
-            "continued": p.continued}
+            "continued": p.continued, "state_writes": p.state_writes}
 
 
 def sieve_probe_smem_atomics(device=0):

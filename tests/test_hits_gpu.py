@@ -138,3 +138,38 @@ def test_batch_hits_equal_closed_form(env):
     counts = torch.empty(len(reqs), dtype=torch.int64, device="cuda")
     got = device_hits(ctx, lambda: S.sieve_batch(ctx, lay, arena, counts))
     assert got == want, (got, want, plan)
+
+
+@pytest.mark.parametrize("l,mant,exp10,n,tune", INTERVALS[:3])
+def test_state_writes_follow_the_plan(env, l, mant, exp10, n, tune):
+    """The state-word count behind the scatter's byte figure: one 8-byte word written back
+    per large prime and scatter group, except in the interval's last group, and in every
+    group once the interval is streamed (its successor reads the last group's words)."""
+    ctx, primes, nsm = env
+    f = S.sieve_f_from_midpoint(l, n, mant, exp10)
+    j0, nbits = f << l, n << l
+    vlast = 2 * (j0 + nbits - 1) + 1
+    cls = tune_class(vlast)
+    saved = S.sieve_get_tuning(ctx, cls)
+    try:
+        if tune:
+            S.sieve_set_tuning(ctx, cls, **tune)
+        t = interval_tuning(ctx, nsm, vlast, nbits)
+        plan = S.sieve_plan_describe(primes, MAX_V, nsm, [(j0, nbits, 0)], tuning=t)
+        assert plan["info"]["run_scatter"] == 1
+        per_group = [g["p_hi"] - g["p_lo"] for g in plan["groups"]]
+        out = torch.empty(nbits // 32, dtype=torch.int32, device="cuda")
+        for streamed in (False, True):
+            S.sieve_set_streaming(ctx, streamed)
+            S.sieve_profile_enable(ctx, True)
+            S.sieve_profile_read(ctx)
+            S.sieve_segments(ctx, l, f, n, out)
+            prof = S.sieve_profile_read(ctx)
+            S.sieve_profile_enable(ctx, False)
+            S.sieve_sync(ctx)
+            assert prof["prime_reads"] == sum(per_group)
+            want = sum(per_group) if streamed else sum(per_group[:-1])
+            assert prof["state_writes"] == want, (streamed, prof["state_writes"], want, len(per_group))
+    finally:
+        S.sieve_set_streaming(ctx, False)
+        S.sieve_set_tuning(ctx, cls, **saved)
